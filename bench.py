@@ -1,0 +1,454 @@
+#!/usr/bin/env python3
+"""Benchmark of the TREE hot path (arXiv 0709.3331, Sec. 2-3) on one GB300.
+
+One bench step = one block of the split-step push: k = 10 electron substeps of
+dt_e = 1e-3 (each: kick, drift, tree build, walk over the electrons; the tenth
+walks every particle), the ion kicks, and the energy/momentum reduction.
+Workload: N = 524,288 (262,144 ions, 262,144 electrons), Gaussian cloud
+sigma = 8, m_i/m_e = 1000, T_e = 1, T_i = 0.01, eps = 0.01, theta = 0.5,
+leaf_cap = 16, FP32 node-relative walk with compensated sums and FP64 state.
+
+Prints one JSON line.  ``value`` = tree-force interactions/s (direct pairs +
+multipole evaluations) over the timed steps, device-timed with CUDA events on
+the context's stream, L2 flushed before every step.  ``e2e`` is the same
+metric through the public API with host buffers: state copied in from pinned
+memory, advanced, energy and state copied back, every step.
+
+``--impl reference`` times the FP64 CPU oracle (the slow, plain reference
+implementation) on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = dict(name="precision_n524288", n=524288, sigma=8.0, seed=3, theta=0.5, eps=0.01,
+                leaf_cap=16, dt_e=1e-3, k=10)
+METRIC = "tree-force interactions/s at N=524288 (FP32 compensated walk, FP64 state)"
+UNIT = "interactions/s"
+# Flops charged per interaction by the roofline (counted from the FP32C kernel's
+# inner loops, FMA = 2, rsqrt = 1): direct pair 20, quadrupole multipole 86.
+FLOP_P2P = 20
+FLOP_M2P = 86
+FP32_LANES_PER_SM = 128
+
+
+def sm_peak_tflops(nsm, mhz):
+    return nsm * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class Clocks:
+    """nvidia-smi samples during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4)
+                          if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def git_rev():
+    try:
+        return subprocess.run(["git", "-C", ROOT, "rev-parse", "--short", "HEAD"],
+                              capture_output=True, text=True, timeout=5).stdout.strip() or None
+    except Exception:
+        return None
+
+
+# --------------------------------------------------------------------- oracle
+def oracle_sample(cloud, n_targets, nthreads, seed=0):
+    """Oracle tree build over all particles + walk over a seeded target sample.
+    Returns (seconds, interactions)."""
+    from oracle import oracle as O
+    rng = np.random.default_rng(seed)
+    tl = np.sort(rng.choice(cloud.n, size=n_targets, replace=False))
+    t0 = time.perf_counter()
+    T = O.Tree(cloud.pos, cloud.species, cloud.q, leaf_cap=WORKLOAD["leaf_cap"])
+    _, _, npp, nmp = T.force(WORKLOAD["theta"], WORKLOAD["eps"], targets=tl, nthreads=nthreads,
+                             counts=True)
+    dt = time.perf_counter() - t0
+    return dt, int(npp.sum() + nmp.sum())
+
+
+def cpu_baseline(cloud, budget_s=15.0):
+    from oracle import oracle as O
+    O.build()
+    cores = os.cpu_count() or 1
+    nthreads = cores if O.has_openmp() else 1
+    dt, inter = oracle_sample(cloud, 2048, nthreads)
+    # scale the target sample so the measured leg takes about budget_s
+    per_target = dt / 2048.0
+    nt = int(min(cloud.n, max(2048, budget_s / max(per_target, 1e-9))))
+    dt, inter = oracle_sample(cloud, nt, nthreads, seed=1)
+    return {"value": inter / dt, "unit": UNIT, "cores": nthreads, "kind": "oracle",
+            "sample": f"FP64 serial-tree oracle: tree build over all {cloud.n} particles + "
+                      f"walk of {nt} seeded targets (theta {WORKLOAD['theta']}, leaf_cap "
+                      f"{WORKLOAD['leaf_cap']}), OpenMP over targets, {dt:.1f} s"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    from paper_0709_3331_gb300.inputs import gaussian_cloud
+    from oracle import oracle as O
+    O.build()
+    c = gaussian_cloud(WORKLOAD["n"], WORKLOAD["sigma"], WORKLOAD["seed"])
+    cores = os.cpu_count() or 1
+    nthreads = cores if O.has_openmp() else 1
+    nt = 4096
+    for _ in range(args.warmup):
+        oracle_sample(c, 512, nthreads)
+    tot_t, tot_i = 0.0, 0
+    for s in range(args.steps):
+        dt, inter = oracle_sample(c, nt, nthreads, seed=100 + s)
+        tot_t += dt
+        tot_i += inter
+    v = tot_i / tot_t
+    sample = (f"per step: FP64 oracle tree build over all {c.n} particles + walk of {nt} "
+              f"seeded targets, OpenMP over targets on {nthreads} threads")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD["name"], "n": c.n,
+                                        "theta": WORKLOAD["theta"], "eps": WORKLOAD["eps"],
+                                        "leaf_cap": WORKLOAD["leaf_cap"]},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": nthreads, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+    return 0
+
+
+# --------------------------------------------------------------------- GPU arm
+def traffic_record():
+    """Per-launch DRAM bytes of the FP32C walk from the committed ncu summary,
+    valid only while the walk source is unchanged since the capture."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "walk_fp32c_traffic.txt")
+    src = os.path.join(ROOT, "paper_0709_3331_gb300", "csrc", "ucp_walk.cu")
+    if not os.path.exists(path):
+        return None
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    rec = {}
+    for line in open(path):
+        if ":" in line:
+            k, v = line.split(":", 1)
+            rec[k.strip()] = v.strip()
+    if rec.get("walk_source_sha256_16") != h:
+        return None
+    try:
+        return float(rec["dram_bytes_per_full_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_0709_3331_gb300 import UCP_FP32C, UCP_FP64, Context
+    from paper_0709_3331_gb300 import build as B
+    from paper_0709_3331_gb300.inputs import gaussian_cloud
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    if rank == 0 or not B.up_to_date():
+        B.build()
+    if ws > 1:
+        dist.barrier()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    W = WORKLOAD
+    c = gaussian_cloud(W["n"], W["sigma"], W["seed"])
+    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+
+    pos_d = torch.from_numpy(c.pos).to(dev)
+    vel_d = torch.from_numpy(c.vel).to(dev)
+    sp_d = torch.from_numpy(c.species).to(dev)
+
+    def timed_steps(ctx, steps, energy=True, profile=True):
+        ctx.stats(reset=True)
+        ctx.profile(profile)
+        ctx.profile_read()
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        energies = []
+        for i in range(steps):
+            flush.zero_()
+            starts[i].record(stream)
+            ctx.step(W["dt_e"], W["k"], W["k"], W["theta"], W["eps"])
+            if energy:
+                energies.append(ctx.energy(W["theta"], W["eps"]))
+            ends[i].record(stream)
+        torch.cuda.synchronize()
+        ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
+        walk_ms, walk_n = ctx.profile_read()
+        ctx.profile(False)
+        st = ctx.stats(reset=True)
+        return ms, st, walk_ms, walk_n, energies
+
+    # ---------------- FP32C headline
+    ctx = Context(c.n, c.q, c.m, leaf_cap=W["leaf_cap"], precision=UCP_FP32C)
+    ctx.set_state(pos_d, vel_d, sp_d)
+    for _ in range(args.warmup):
+        ctx.step(W["dt_e"], W["k"], W["k"], W["theta"], W["eps"])
+        ctx.energy(W["theta"], W["eps"])
+    torch.cuda.synchronize()
+    clk = Clocks(local)
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk.start()
+    t_wall0 = time.perf_counter()
+    ms, st, walk_ms, walk_n, energies = timed_steps(ctx, args.steps)
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall0
+    clocks = clk.stop()
+    inter = int(st[0] + st[1])
+    launches = int(st[6])
+    if ws > 1:
+        t = torch.tensor([ms, float(inter)], dtype=torch.float64, device=dev)
+        tmax = t.clone()
+        dist.all_reduce(tmax[:1], op=dist.ReduceOp.MAX)
+        dist.all_reduce(t[1:], op=dist.ReduceOp.SUM)
+        ms_all, inter_all = float(tmax[0]), float(t[1])
+    else:
+        ms_all, inter_all = ms, float(inter)
+    value = inter_all / (ms_all / 1e3)
+    pst = W["n"] * W["k"] * args.steps * ws / (ms_all / 1e3)
+
+    # roofline of the dominant kernel (the FP32C walk), flops per launch / launch time
+    flops = FLOP_P2P * float(st[0]) + FLOP_M2P * float(st[1])
+    achieved = flops / (walk_ms / 1e3) / 1e12 if walk_ms > 0 else None
+    peak_mhz = 2070.0
+    peak = sm_peak_tflops(nsm, peak_mhz)
+    traffic = traffic_record()
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": (achieved / peak) if achieved else None,
+                "traffic": traffic, "kernel": "k_walk_fp32c",
+                "peak_basis": f"FP32 pipe: {nsm} SMs x 128 lanes x 2 flop x {peak_mhz:.0f} MHz "
+                              "(max SM clock); flops = 20 per direct pair + 86 per multipole",
+                "walk_ms_per_launch": walk_ms / max(walk_n, 1), "walk_launches": walk_n,
+                "walk_share_of_step": walk_ms / ms if ms > 0 else None}
+
+    # ---------------- e2e through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(c, W, args, ws, dev, flush, Context, UCP_FP32C)
+
+    # ---------------- FP64 walk and theta sweep (context lines, fewer steps)
+    extra = {}
+    if not args.quick:
+        extra = run_extras(c, W, ws, pos_d, vel_d, sp_d, Context, UCP_FP32C, UCP_FP64,
+                           timed_steps, flush, stream, peak, ms / args.steps)
+
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_all / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 walk (compensated), f64 state",
+        "data": "synthetic",
+        "config": {"workload": W["name"], "n": W["n"], "sigma": W["sigma"], "theta": W["theta"],
+                   "eps": W["eps"], "leaf_cap": W["leaf_cap"], "dt_e": W["dt_e"],
+                   "ion_substep_ratio": W["k"], "step": "one block of 10 electron substeps",
+                   "parallelism": f"replicas x{ws}", "l2": "flushed (256 MB write) before "
+                                                         "every timed step"},
+        "particle_steps_per_s": pst,
+        "p2p_pairs_per_s": float(st[0]) * ws / (ms_all / 1e3),
+        "m2p_evals_per_s": float(st[1]) * ws / (ms_all / 1e3),
+        "interactions_per_target_walk": {"p2p": float(st[0]) / max(int(st[2]), 1),
+                                         "m2p": float(st[1]) / max(int(st[2]), 1)},
+        "roofline": roofline,
+        "clocks": clocks,
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "energy_last": energies[-1].tolist() if energies else None,
+        "wall_s_timed_region": t_wall,
+        "git": git_rev(),
+    }
+    out.update(extra)
+    ctx.close()
+    if rank == 0 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(c)
+    if rank == 0:
+        print(json.dumps(out))
+    if ws > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def run_e2e(c, W, args, ws, dev, flush, Context, UCP_FP32C):
+    import torch
+    import torch.distributed as dist
+    pin_pos = torch.from_numpy(c.pos).pin_memory()
+    pin_vel = torch.from_numpy(c.vel).pin_memory()
+    pin_sp = torch.from_numpy(c.species).pin_memory()
+    out_pos = torch.empty((c.n, 3), dtype=torch.float64).pin_memory()
+    out_vel = torch.empty((c.n, 3), dtype=torch.float64).pin_memory()
+    ctx_h = Context(c.n, c.q, c.m, leaf_cap=W["leaf_cap"], precision=UCP_FP32C)
+    np_pos, np_vel, np_sp = pin_pos.numpy(), pin_vel.numpy(), pin_sp.numpy()
+    np_opos, np_ovel = out_pos.numpy(), out_vel.numpy()
+    for _ in range(max(1, args.warmup)):
+        ctx_h.set_state(np_pos, np_vel, np_sp)
+        ctx_h.step(W["dt_e"], W["k"], W["k"], W["theta"], W["eps"])
+        ctx_h.energy(W["theta"], W["eps"])
+        ctx_h.get_state(np_opos, np_ovel)
+    ctx_h.stats(reset=True)
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    e0 = time.perf_counter()
+    e_steps = max(1, args.steps)
+    for _ in range(e_steps):
+        flush.zero_()
+        ctx_h.set_state(np_pos, np_vel, np_sp)
+        ctx_h.step(W["dt_e"], W["k"], W["k"], W["theta"], W["eps"])
+        ctx_h.energy(W["theta"], W["eps"])
+        ctx_h.get_state(np_opos, np_ovel)
+    torch.cuda.synchronize()
+    e_t = time.perf_counter() - e0
+    st_h = ctx_h.stats(reset=True)
+    e_val = float(st_h[0] + st_h[1]) / e_t
+    if ws > 1:
+        t = torch.tensor([e_t, float(st_h[0] + st_h[1])], dtype=torch.float64, device=dev)
+        tm = t.clone()
+        dist.all_reduce(tm[:1], op=dist.ReduceOp.MAX)
+        dist.all_reduce(t[1:], op=dist.ReduceOp.SUM)
+        e_val = float(t[1]) / float(tm[0])
+    e2e = {"value": e_val, "unit": UNIT,
+           "h2d_bytes_per_step": int(c.pos.nbytes + c.vel.nbytes + c.species.nbytes),
+           "d2h_bytes_per_step": int(c.pos.nbytes + c.vel.nbytes + 6 * 8),
+           "note": "per step: set_state from pinned host arrays (forces recomputed from the "
+                   "copied state), one block step, energy, get_state to host"}
+    ctx_h.close()
+    return e2e
+
+
+def run_extras(c, W, ws, pos_d, vel_d, sp_d, Context, UCP_FP32C, UCP_FP64, timed_steps, flush,
+               stream, peak, ms_step32):
+    import torch
+    extra = {}
+    ctx64 = Context(c.n, c.q, c.m, leaf_cap=W["leaf_cap"], precision=UCP_FP64)
+    ctx64.set_state(pos_d, vel_d, sp_d)
+    ctx64.step(W["dt_e"], W["k"], W["k"], W["theta"], W["eps"])
+    torch.cuda.synchronize()
+    ms64, st64, wms64, wn64, _ = timed_steps(ctx64, 1)
+    extra["fp64"] = {"value": float(st64[0] + st64[1]) / (ms64 / 1e3), "unit": UNIT,
+                     "ms_per_step": ms64, "walk_ms_per_launch": wms64 / max(wn64, 1),
+                     "speedup_fp32c_over_fp64": ms64 / ms_step32}
+    ctx64.close()
+    sweep = {}
+    for th in (0.3, 0.5, 0.7):
+        cs = Context(c.n, c.q, c.m, leaf_cap=W["leaf_cap"], precision=UCP_FP32C)
+        cs.set_state(pos_d, vel_d, sp_d)
+        cs.step(W["dt_e"], W["k"], W["k"], th, W["eps"])
+        torch.cuda.synchronize()
+        cs.stats(reset=True)
+        cs.profile(True)
+        cs.profile_read()
+        e_a = torch.cuda.Event(enable_timing=True)
+        e_b = torch.cuda.Event(enable_timing=True)
+        flush.zero_()
+        e_a.record(stream)
+        cs.step(W["dt_e"], W["k"], W["k"], th, W["eps"])
+        e_b.record(stream)
+        torch.cuda.synchronize()
+        m1 = e_a.elapsed_time(e_b)
+        wm, wn = cs.profile_read()
+        s1 = cs.stats(reset=True)
+        fl = FLOP_P2P * float(s1[0]) + FLOP_M2P * float(s1[1])
+        sweep[str(th)] = {"interactions_per_s": float(s1[0] + s1[1]) / (m1 / 1e3),
+                          "ms_per_step": m1,
+                          "particle_steps_per_s": W["n"] * W["k"] / (m1 / 1e3),
+                          "p2p_per_target": float(s1[0]) / max(int(s1[2]), 1),
+                          "m2p_per_target": float(s1[1]) / max(int(s1[2]), 1),
+                          "walk_frac_fp32_peak": fl / (wm / 1e3) / 1e12 / peak}
+        cs.close()
+    extra["theta_sweep"] = sweep
+    return extra
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--quick", action="store_true", help="skip the FP64 and theta-sweep lines")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer e2e leg")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "gpu":
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,149 @@
+/*
+ * ucp.h -- C ABI of the GB300 two-component plasma TREE library (libucp.so).
+ *
+ * The library evaluates the Coulomb force on the electrons and ions of an
+ * open-boundary two-component plasma with the TREE method of Jeon, Kress,
+ * Collins and Gronbech-Jensen (arXiv 0709.3331), Sec. 3, and advances the
+ * particles with the velocity Verlet push of Sec. 2, electrons on a short
+ * substep and ions on k of them.  One context = one particle set on one GPU.
+ *
+ * Conventions for every call:
+ *   - Return 0 (UCP_OK) on success or a negative UCP_E* code; no call throws
+ *     or aborts.  ucp_strerror() names the code; ucp_last_error() returns a
+ *     message about the most recent failure in this context.
+ *   - Arrays are in the caller's particle order (index i = the i-th particle
+ *     handed to ucp_set_state); the library keeps its own copy in key order.
+ *   - pos / vel / acc are N x 3 row-major double (x, y, z of particle 0 first).
+ *   - on_device = 1: the pointer is CUDA device memory (e.g. a torch CUDA
+ *     tensor's data_ptr) read or written in stream order on the context's
+ *     stream and the call returns after enqueueing.  on_device = 0: host
+ *     memory; the call copies and synchronises the stream before returning.
+ *   - Units are reduced: Coulomb constant 1 (Eq. 2 with e^2/(4 pi eps0) = 1),
+ *     so the pair potential is q_i q_j / sqrt(r^2 + eps^2) (Eq. 1 with
+ *     Plummer softening eps).
+ *   - A context is not thread-safe; different contexts are independent.
+ *   - The caller owns every pointer it passes; the library owns the context
+ *     and the device memory it allocates in ucp_create (freed by ucp_destroy).
+ */
+#ifndef UCP_H
+#define UCP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    UCP_OK = 0,
+    UCP_EINVAL = -1,      /* bad argument (null pointer, size, theta, eps, dt, k) */
+    UCP_ENOMEM = -2,      /* device or host allocation failed */
+    UCP_ECUDA = -3,       /* a CUDA runtime call or kernel launch failed */
+    UCP_ENONFINITE = -4,  /* a position or velocity is NaN or infinite */
+    UCP_ETIMEOUT = -5,    /* a bounded device-side wait gave up */
+    UCP_ESTATE = -6       /* call order: no state set yet */
+};
+
+enum { UCP_FP64 = 0, UCP_FP32C = 1 };  /* arithmetic of the force walk */
+enum { UCP_ION = 0, UCP_ELECTRON = 1 }; /* species codes */
+
+typedef struct ucp_ctx ucp_ctx;
+
+typedef struct {
+    int64_t n;          /* particles, 1 <= n <= 2^31 - 1 */
+    int32_t leaf_cap;   /* a box with at most leaf_cap particles is a leaf
+                           (Sec. 3 subdivides "until every box contains no more
+                           than one particle": leaf_cap = 1); 1..1024 */
+    int32_t precision;  /* UCP_FP64 or UCP_FP32C (FP32 node-relative arithmetic,
+                           compensated sums, FP64 state and results) */
+    double q[2];        /* charge per species [ion, electron] */
+    double m[2];        /* mass per species, > 0 */
+    void* cuda_stream;  /* cudaStream_t the context works on (NULL = legacy) */
+} ucp_params;
+
+/* Create a context for params->n particles and allocate all device memory
+ * it will need (nothing is allocated later).  *out is set on success. */
+int ucp_create(ucp_ctx** out, const ucp_params* params);
+
+/* Free the context and its device memory (NULL is allowed). */
+void ucp_destroy(ucp_ctx* ctx);
+
+/* Copy in positions, velocities (N x 3) and species (N, values 0 or 1).
+ * Rejects non-finite values with UCP_ENONFINITE and species outside {0,1}
+ * with UCP_EINVAL.  Invalidates the tree and the stored accelerations and
+ * resets the step counter. */
+int ucp_set_state(ucp_ctx* ctx, const double* pos, const double* vel,
+                  const int8_t* species, int on_device);
+
+/* Copy out positions and velocities in the caller's order (either may be NULL). */
+int ucp_get_state(ucp_ctx* ctx, double* pos, double* vel, int on_device);
+
+/* Sec. 3 TREE construction on the current positions: enclosing cube, Morton
+ * keys (21 bits per axis), stable key sort (ties by particle index), octree
+ * boxes as key prefixes in pre-order, and moments of every box (monopole,
+ * |q|-weighted centroid, dipole, second moment). */
+int ucp_tree_build(ucp_ctx* ctx);
+
+/* Sec. 3 particle-TREE interaction on every particle with the opening
+ * criterion of Eq. 5 (s/theta + delta < d; 0 <= theta <= 1) and softening
+ * eps >= 0.  Builds the tree first if the positions changed since the last
+ * build.  acc (N x 3, = q_t E_t / m_t) and phi (N, potential at the
+ * particle, no self term) may each be NULL.  Also stores the accelerations
+ * for a following ucp_step. */
+int ucp_tree_force(ucp_ctx* ctx, double theta, double eps, double* acc, double* phi,
+                   int on_device);
+
+/* Sec. 2 velocity Verlet with electron substeps: n_electron_steps / k blocks
+ * (n_electron_steps must be a multiple of k = ion_substep_ratio >= 1).  One
+ * block, dt_i = k dt_e:
+ *   ions v += dt_i/2 a;  k times { electrons v += dt_e/2 a; all x += dt_e v;
+ *   rebuild the tree; a of the electrons (of every particle on the k-th);
+ *   electrons v += dt_e/2 a };  ions v += dt_i/2 a.
+ * k = 1 is plain velocity Verlet.  Accelerations of the current positions
+ * are computed first when none are stored. */
+int ucp_step(ucp_ctx* ctx, double dt_e, int ion_substep_ratio, int64_t n_electron_steps,
+             double theta, double eps);
+
+/* Sec. 5 observables of the current state: out = {KE_ion, KE_electron, PE,
+ * E = KE + PE, |P| (total momentum), electron steps taken}.  PE is
+ * (1/2) sum_t q_t phi_t with the tree potential; the walk over all particles
+ * that ends every ucp_step block already leaves phi, so after a step with the
+ * same theta and eps this is a reduction only, otherwise one walk runs first. */
+int ucp_energy(ucp_ctx* ctx, double theta, double eps, double out[6]);
+
+/* Counters: out = {direct pairs, multipole evaluations, walk targets, walk
+ * launches} summed since the last reset, {boxes, deepest depth} of the last
+ * tree, {CUDA kernels launched by this library (all contexts of the process)
+ * since the last reset, 0}.  reset != 0 zeroes the summed counters after
+ * reading. */
+int ucp_stats(ucp_ctx* ctx, int64_t out[8], int reset);
+
+/* Inspection of the last build (tests): enclosing cube {centre xyz, side};
+ * key-sorted 63-bit Morton keys and the caller index of each sorted slot;
+ * box table in pre-order (host arrays of capacity cap >= *nnodes, else
+ * UCP_EINVAL with *nnodes set): topo (cap x 4 int32 {begin, end, next,
+ * depth}; begin/end index key-sorted slots, next = first box after the
+ * subtree), is_leaf (cap int8), geom (cap x 20 double {centre xyz, side, S0,
+ * M, c xyz, D xyz, Q xx xy xz yy yz zz, delta, 0}); any array may be NULL.
+ * ucp_get_counts: direct pairs and multipole evaluations per particle in the
+ * last walk, in the caller's order (0 for particles that were not targets). */
+int ucp_get_cube(ucp_ctx* ctx, double out[4]);
+int ucp_get_sorted(ucp_ctx* ctx, uint64_t* keys, uint32_t* ids, int on_device);
+int ucp_get_tree(ucp_ctx* ctx, int64_t* nnodes, int64_t cap, int32_t* topo,
+                 int8_t* is_leaf, double* geom);
+int ucp_get_counts(ucp_ctx* ctx, int32_t* p2p, int32_t* m2p, int on_device);
+
+/* Kernel timing: when enabled, the walk kernels are bracketed by CUDA events
+ * on the context's stream; read returns {total ms, launches} of the walk since
+ * the last read (synchronises the stream). */
+int ucp_profile(ucp_ctx* ctx, int enable);
+int ucp_profile_read(ucp_ctx* ctx, double* walk_ms, int64_t* walk_launches);
+
+const char* ucp_strerror(int code);
+const char* ucp_last_error(ucp_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* UCP_H */

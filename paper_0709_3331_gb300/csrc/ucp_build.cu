@@ -1,0 +1,653 @@
+// ucp_build.cu -- TREE construction of Sec. 3 (arXiv 0709.3331) on the GPU:
+// enclosing cube, Morton keys, stable radix sort, box topology as key
+// prefixes in pre-order, and box moments bottom-up.
+//
+// Arithmetic that decides an integer (cube, cell coordinates, box centre) is
+// written with explicit round-to-nearest intrinsics in the order of the
+// definition, so that no multiply-add contraction changes a cell.
+#include "ucp_internal.cuh"
+
+#include <math.h>
+
+namespace ucp {
+
+namespace {
+
+constexpr int kScanThreads = 1024;
+constexpr int kScanItems = 4;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+__device__ __forceinline__ int warp_incl_scan(int v, int lane)
+{
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int u = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += u;
+    }
+    return v;
+}
+
+// Exclusive scan of one value per thread over a block of kScanThreads.
+__device__ int block_excl_scan(int v, int* total)
+{
+    __shared__ int warp_sums[32];
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int inc = warp_incl_scan(v, lane);
+    if (lane == 31) warp_sums[w] = inc;
+    __syncthreads();
+    if (w == 0) {
+        int nw = blockDim.x >> 5;
+        int s = lane < nw ? warp_sums[lane] : 0;
+        int si = warp_incl_scan(s, lane);
+        if (lane < nw) warp_sums[lane] = si - s;
+        if (lane == 31) *total = si;
+    }
+    __syncthreads();
+    int r = warp_sums[w] + inc - v;
+    __syncthreads();
+    return r;
+}
+
+__global__ void k_scan_reduce(const int* __restrict__ in, int n, int* __restrict__ part)
+{
+    int base = blockIdx.x * kScanTile;
+    int s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        int i = base + threadIdx.x * kScanItems + k;
+        if (i < n) s += in[i];
+    }
+    __shared__ int tot;
+    block_excl_scan(s, &tot);
+    if (threadIdx.x == 0) part[blockIdx.x] = tot;
+}
+
+__global__ void k_scan_partials(int* part, int nb, int* total)
+{
+    // one block: each thread scans a contiguous chunk of the partials
+    int per = (nb + blockDim.x - 1) / blockDim.x;
+    int b0 = threadIdx.x * per;
+    int s = 0;
+    for (int b = b0; b < b0 + per && b < nb; ++b) s += part[b];
+    __shared__ int tot;
+    int off = block_excl_scan(s, &tot);
+    for (int b = b0; b < b0 + per && b < nb; ++b) {
+        int v = part[b];
+        part[b] = off;
+        off += v;
+    }
+    if (threadIdx.x == 0 && total) *total = tot;
+}
+
+__global__ void k_scan_apply(const int* __restrict__ in, int* __restrict__ out, int n,
+                             const int* __restrict__ part)
+{
+    int base = blockIdx.x * kScanTile;
+    int v[kScanItems];
+    int s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        int i = base + threadIdx.x * kScanItems + k;
+        v[k] = i < n ? in[i] : 0;
+        s += v[k];
+    }
+    __shared__ int tot;
+    int off = block_excl_scan(s, &tot) + part[blockIdx.x];
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        int i = base + threadIdx.x * kScanItems + k;
+        if (i < n) out[i] = off;
+        off += v[k];
+    }
+}
+
+// ---------------------------------------------------------------- cube
+__global__ void k_bbox_partial(const double* __restrict__ x, const double* __restrict__ y,
+                               const double* __restrict__ z, int n, double* __restrict__ part)
+{
+    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        double v[3] = {x[i], y[i], z[i]};
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            lo[a] = fmin(lo[a], v[a]);
+            hi[a] = fmax(hi[a], v[a]);
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            lo[a] = fmin(lo[a], __shfl_xor_sync(0xffffffffu, lo[a], o));
+            hi[a] = fmax(hi[a], __shfl_xor_sync(0xffffffffu, hi[a], o));
+        }
+    __shared__ double s[32][6];
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0)
+        for (int a = 0; a < 3; ++a) {
+            s[w][a] = lo[a];
+            s[w][3 + a] = hi[a];
+        }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int ww = 1; ww < (int)(blockDim.x >> 5); ++ww)
+            for (int a = 0; a < 3; ++a) {
+                s[0][a] = fmin(s[0][a], s[ww][a]);
+                s[0][3 + a] = fmax(s[0][3 + a], s[ww][3 + a]);
+            }
+        for (int a = 0; a < 6; ++a) part[blockIdx.x * 6 + a] = s[0][a];
+    }
+}
+
+// Sec. 3: the cube that encloses every particle.  Centre = (min + max) / 2 per
+// axis; side = largest extent * (1 + 2^-20) so that the maximum falls inside;
+// side 1 when all particles coincide.
+__global__ void k_bbox_final(const double* __restrict__ part, int nblk, Cube* cube)
+{
+    if (threadIdx.x != 0) return;
+    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int b = 0; b < nblk; ++b)
+        for (int a = 0; a < 3; ++a) {
+            lo[a] = fmin(lo[a], part[6 * b + a]);
+            hi[a] = fmax(hi[a], part[6 * b + 3 + a]);
+        }
+    double ext = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        cube->c[a] = __dmul_rn(__dadd_rn(lo[a], hi[a]), 0.5);
+        double e = __dsub_rn(hi[a], lo[a]);
+        if (e > ext) ext = e;
+    }
+    cube->L = ext > 0.0 ? __dmul_rn(ext, 1.0 + 0x1p-20) : 1.0;
+}
+
+// ---------------------------------------------------------------- keys
+__device__ __forceinline__ unsigned long long spread3(unsigned int v)
+{
+    unsigned long long x = v & 0x1fffffu;
+    x = (x | (x << 32)) & 0x001f00000000ffffull;
+    x = (x | (x << 16)) & 0x001f0000ff0000ffull;
+    x = (x | (x << 8)) & 0x100f00f00f00f00full;
+    x = (x | (x << 4)) & 0x10c30c30c30c30c3ull;
+    x = (x | (x << 2)) & 0x1249249249249249ull;
+    return x;
+}
+
+__device__ __forceinline__ unsigned int cell_coord(double x, double c, double L)
+{
+    double lo = __dsub_rn(c, __dmul_rn(L, 0.5));
+    double u = floor(__dmul_rn(__ddiv_rn(__dsub_rn(x, lo), L), 2097152.0));
+    if (!(u > 0.0)) return 0u;
+    if (u >= 2097151.0) return 2097151u;
+    return (unsigned int)u;
+}
+
+__global__ void k_keys(const double* __restrict__ x, const double* __restrict__ y,
+                       const double* __restrict__ z, int n, const Cube* __restrict__ cube,
+                       unsigned long long* __restrict__ key, unsigned int* __restrict__ val)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double L = cube->L;
+    unsigned int kx = cell_coord(x[i], cube->c[0], L);
+    unsigned int ky = cell_coord(y[i], cube->c[1], L);
+    unsigned int kz = cell_coord(z[i], cube->c[2], L);
+    key[i] = spread3(kx) | (spread3(ky) << 1) | (spread3(kz) << 2);
+    val[i] = (unsigned int)i;
+}
+
+// ---------------------------------------------------------------- sort
+constexpr int kSortThreads = 256;
+constexpr int kSortWarps = kSortThreads / 32;
+constexpr int kSortChunks = 8;                              // 32-key chunks per warp
+constexpr int kSortTile = kSortThreads * kSortChunks;       // 2048 keys per block
+constexpr int kRadix = 256;
+
+__global__ void __launch_bounds__(kSortThreads)
+k_radix_hist(const unsigned long long* __restrict__ key, int n, int shift,
+             unsigned int* __restrict__ hist)
+{
+    __shared__ unsigned int cnt[kRadix];
+    cnt[threadIdx.x] = 0;
+    __syncthreads();
+    int base = blockIdx.x * kSortTile;
+#pragma unroll
+    for (int k = 0; k < kSortChunks; ++k) {
+        int i = base + k * kSortThreads + threadIdx.x;
+        if (i < n) atomicAdd(&cnt[(unsigned int)(key[i] >> shift) & 0xffu], 1u);
+    }
+    __syncthreads();
+    hist[threadIdx.x * gridDim.x + blockIdx.x] = cnt[threadIdx.x];
+}
+
+// Stable scatter: warp w owns the contiguous sub-tile [w*256, w*256+256) of the
+// block's tile and ranks its keys chunk by chunk in order with match_any, so
+// equal digits keep their input order.
+__global__ void __launch_bounds__(kSortThreads)
+k_radix_scatter(const unsigned long long* __restrict__ kin, const unsigned int* __restrict__ vin,
+                unsigned long long* __restrict__ kout, unsigned int* __restrict__ vout, int n,
+                int shift, const unsigned int* __restrict__ off)
+{
+    __shared__ int cnt[kSortWarps][kRadix];
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int d = lane; d < kRadix; d += 32) cnt[w][d] = 0;
+    __syncwarp();
+    int base = blockIdx.x * kSortTile + w * (kSortTile / kSortWarps);
+    unsigned long long kk[kSortChunks];
+    unsigned int vv[kSortChunks];
+    int dig[kSortChunks], rank[kSortChunks];
+    unsigned int lt = (1u << lane) - 1u;
+#pragma unroll
+    for (int c = 0; c < kSortChunks; ++c) {
+        int i = base + c * 32 + lane;
+        bool ok = i < n;
+        kk[c] = ok ? kin[i] : 0ull;
+        vv[c] = ok ? vin[i] : 0u;
+        int d = ok ? (int)((kk[c] >> shift) & 0xffu) : kRadix + lane;  // invalid lanes unique
+        dig[c] = d;
+        unsigned int peers = __match_any_sync(0xffffffffu, d);
+        int leader = __ffs(peers) - 1;
+        int before = 0;
+        if (ok && lane == leader) {
+            before = cnt[w][d];
+            cnt[w][d] = before + __popc(peers);
+        }
+        before = __shfl_sync(0xffffffffu, before, leader);
+        rank[c] = before + __popc(peers & lt);
+        __syncwarp();
+    }
+    __syncthreads();
+    // exclusive scan over warps per digit, plus the block's global offset
+    {
+        int d = threadIdx.x;  // kSortThreads == kRadix
+        unsigned int run = off[d * gridDim.x + blockIdx.x];
+        for (int ww = 0; ww < kSortWarps; ++ww) {
+            int t = cnt[ww][d];
+            cnt[ww][d] = (int)run;
+            run += t;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int c = 0; c < kSortChunks; ++c) {
+        int i = base + c * 32 + lane;
+        if (i < n) {
+            int p = cnt[w][dig[c]] + rank[c];
+            kout[p] = kk[c];
+            vout[p] = vv[c];
+        }
+    }
+}
+
+// Equal keys must come out ordered by caller index (ties by particle index):
+// the run starting at i is insertion-sorted by ids[perm[.]].  Runs are rare and
+// short except when particles coincide (depth-21 boxes).
+__global__ void k_tiefix(const unsigned long long* __restrict__ key, unsigned int* __restrict__ perm,
+                         const unsigned int* __restrict__ ids, int n)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n - 1) return;
+    unsigned long long k = key[i];
+    if (key[i + 1] != k || (i > 0 && key[i - 1] == k)) return;
+    int e = i + 1;
+    while (e < n && key[e] == k) ++e;
+    for (int a = i + 1; a < e; ++a) {
+        unsigned int pv = perm[a];
+        unsigned int idv = ids[pv];
+        int b = a - 1;
+        while (b >= i && ids[perm[b]] > idv) {
+            perm[b + 1] = perm[b];
+            --b;
+        }
+        perm[b + 1] = pv;
+    }
+}
+
+// ---------------------------------------------------------------- topology
+__device__ __forceinline__ unsigned long long prefix_at(unsigned long long k, int d)
+{
+    return d == 0 ? 0ull : (k >> (3 * (kMaxDepth - d)));
+}
+
+// first j > i whose depth-d prefix differs from key[i]'s (or n)
+__device__ int box_end(const unsigned long long* __restrict__ K, int n, int i, int d)
+{
+    if (d == 0) return n;
+    unsigned long long p = prefix_at(K[i], d);
+    int lo = i, step = 1, hi = i + 1;
+    while (hi < n && prefix_at(K[hi], d) == p) {
+        lo = hi;
+        step <<= 1;
+        hi = i + step;
+    }
+    if (hi > n) hi = n;
+    while (hi - lo > 1) {
+        int mid = lo + ((hi - lo) >> 1);
+        if (prefix_at(K[mid], d) == p) lo = mid;
+        else hi = mid;
+    }
+    return hi;
+}
+
+// first j <= i whose depth-d prefix equals key[i]'s
+__device__ int box_begin(const unsigned long long* __restrict__ K, int i, int d)
+{
+    if (d == 0) return 0;
+    unsigned long long p = prefix_at(K[i], d);
+    int hi = i, step = 1, lo = i - 1;
+    while (lo >= 0 && prefix_at(K[lo], d) == p) {
+        hi = lo;
+        step <<= 1;
+        lo = i - step;
+    }
+    if (lo < -1) lo = -1;
+    while (hi - lo > 1) {
+        int mid = lo + ((hi - lo) >> 1);
+        if (prefix_at(K[mid], d) == p) hi = mid;
+        else lo = mid;
+    }
+    return hi;
+}
+
+// depth of the first box that starts at sorted position i (22 = none)
+__device__ __forceinline__ int first_depth(const unsigned long long* __restrict__ K, int i)
+{
+    if (i == 0) return 0;
+    unsigned long long x = K[i] ^ K[i - 1];
+    if (x == 0ull) return kMaxDepth + 1;
+    return (__clzll((long long)x) - 1) / 3 + 1;
+}
+
+// Every box is a key prefix; the boxes that start at sorted position i are
+// those of depth >= first_depth(i) down to the first leaf.  A box exists iff
+// its parent holds more than leaf_cap particles.  Emitting boxes in order of
+// (start position, depth) gives pre-order with children in octant order.
+__global__ void k_topo_count(const unsigned long long* __restrict__ K, int n, int leaf_cap,
+                             int* __restrict__ cnt)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int d0 = first_depth(K, i);
+    int c = 0;
+    if (d0 <= kMaxDepth) {
+        bool ok = true;
+        if (d0 > 0) {
+            int pb = box_begin(K, i, d0 - 1), pe = box_end(K, n, i, d0 - 1);
+            ok = pe - pb > leaf_cap;
+        }
+        if (ok)
+            for (int d = d0; d <= kMaxDepth; ++d) {
+                int e = box_end(K, n, i, d);
+                ++c;
+                if (e - i <= leaf_cap || d == kMaxDepth) break;
+            }
+    }
+    cnt[i] = c;
+}
+
+__global__ void k_topo_emit(const unsigned long long* __restrict__ K, int n, int leaf_cap,
+                            const int* __restrict__ cnt, const int* __restrict__ off, Tree t)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int c = cnt[i];
+    if (c == 0) return;
+    int nn = *t.nnodes;
+    int d0 = first_depth(K, i);
+    int node = off[i];
+    int parent = -1;
+    if (d0 > 0) {
+        int pb = box_begin(K, i, d0 - 1);
+        parent = off[pb] + (d0 - 1 - first_depth(K, pb));
+    }
+    int dmax = 0;
+    for (int j = 0; j < c; ++j) {
+        int d = d0 + j;
+        int e = box_end(K, n, i, d);
+        bool leaf = (e - i <= leaf_cap) || d == kMaxDepth;
+        int nx = e < n ? off[e] : nn;
+        if (node >= t.cap) break;  // cannot happen: the capacity bounds the box count
+        t.info[node] = make_int4(i, e, nx, parent);
+        t.depth_leaf[node] = d | (leaf ? 256 : 0);
+        t.cell[node] = prefix_at(K[i], d);
+        t.arrive[node] = 0;
+        parent = node;
+        ++node;
+        dmax = d;
+    }
+    atomicMax(t.maxdepth, dmax);
+}
+
+// ---------------------------------------------------------------- moments
+__device__ __forceinline__ unsigned int compact3(unsigned long long x)
+{
+    x &= 0x1249249249249249ull;
+    x = (x | (x >> 2)) & 0x10c30c30c30c30c3ull;
+    x = (x | (x >> 4)) & 0x100f00f00f00f00full;
+    x = (x | (x >> 8)) & 0x001f0000ff0000ffull;
+    x = (x | (x >> 16)) & 0x001f00000000ffffull;
+    x = (x | (x >> 32)) & 0x1fffffull;
+    return (unsigned int)x;
+}
+
+// geometric box centre: lo + (cell + 1/2) * side, side = L 2^-depth
+__device__ __forceinline__ void box_centre(const Cube& cb, unsigned long long cell, int d,
+                                           double ctr[3], double* side)
+{
+    double s = ldexp(cb.L, -d);
+    *side = s;
+    unsigned int ic[3] = {compact3(cell), compact3(cell >> 1), compact3(cell >> 2)};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        double lo = __dsub_rn(cb.c[a], __dmul_rn(cb.L, 0.5));
+        ctr[a] = __dadd_rn(lo, __dmul_rn(__dadd_rn((double)ic[a], 0.5), s));
+    }
+}
+
+__device__ void finish_box(double* __restrict__ m, const double ctr[3])
+{
+    double ex = __dsub_rn(m[MC + 0], ctr[0]);
+    double ey = __dsub_rn(m[MC + 1], ctr[1]);
+    double ez = __dsub_rn(m[MC + 2], ctr[2]);
+    m[MDELTA] = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)),
+                                     __dmul_rn(ez, ez)));
+}
+
+// Moments of each leaf from its particles; a box is finished by the last of
+// its children to complete (arrival counted in particles), which combines the
+// children's moments about the box's own centroid (parallel-axis shift).
+__global__ void k_moments(const double* __restrict__ x, const double* __restrict__ y,
+                          const double* __restrict__ z, const int8_t* __restrict__ sp,
+                          const double* __restrict__ qsp, const Cube* __restrict__ cube, Tree t,
+                          float4* __restrict__ src32, int want_f32)
+{
+    int nn = *t.nnodes;
+    Cube cb = *cube;
+    double q0 = qsp[0], q1 = qsp[1];
+    for (int node = blockIdx.x * blockDim.x + threadIdx.x; node < nn;
+         node += gridDim.x * blockDim.x) {
+        int dl = t.depth_leaf[node];
+        if (!(dl & 256)) continue;
+        int4 inf = t.info[node];
+        double ctr[3], side;
+        box_centre(cb, t.cell[node], dl & 255, ctr, &side);
+        double S0 = 0.0, M = 0.0, w[3] = {0.0, 0.0, 0.0};
+        for (int j = inf.x; j < inf.y; ++j) {
+            double qj = sp[j] ? q1 : q0;
+            double aq = fabs(qj);
+            S0 += aq;
+            M += qj;
+            w[0] += aq * x[j];
+            w[1] += aq * y[j];
+            w[2] += aq * z[j];
+        }
+        double c[3];
+        for (int a = 0; a < 3; ++a) c[a] = S0 > 0.0 ? w[a] / S0 : ctr[a];
+        double D[3] = {0, 0, 0}, Q[6] = {0, 0, 0, 0, 0, 0};
+        for (int j = inf.x; j < inf.y; ++j) {
+            double qj = sp[j] ? q1 : q0;
+            double yx = x[j] - c[0], yy = y[j] - c[1], yz = z[j] - c[2];
+            D[0] += qj * yx;
+            D[1] += qj * yy;
+            D[2] += qj * yz;
+            Q[0] += qj * yx * yx;
+            Q[1] += qj * yx * yy;
+            Q[2] += qj * yx * yz;
+            Q[3] += qj * yy * yy;
+            Q[4] += qj * yy * yz;
+            Q[5] += qj * yz * yz;
+            if (want_f32) {
+                float ox = (float)yx, oy = (float)yy, oz = (float)yz;
+                src32[j] = make_float4(ox, oy, oz, (float)qj);
+            }
+        }
+        double* m = t.mom + (size_t)node * kMom;
+        m[MC + 0] = c[0];
+        m[MC + 1] = c[1];
+        m[MC + 2] = c[2];
+        m[MM] = M;
+        for (int a = 0; a < 3; ++a) m[MD + a] = D[a];
+        for (int a = 0; a < 6; ++a) m[MQ + a] = Q[a];
+        m[MS0] = S0;
+        finish_box(m, ctr);
+
+        // climb: the child that completes a box's particle count finishes it
+        int cur = node, cnt = inf.y - inf.x;
+        while (true) {
+            int p = t.info[cur].w;
+            if (p < 0) break;
+            int4 pin = t.info[p];
+            int pc = pin.y - pin.x;
+            __threadfence();
+            int old = atomicAdd(&t.arrive[p], cnt);
+            if (old + cnt != pc) break;
+            __threadfence();
+            double S = 0.0, MM_ = 0.0, ww[3] = {0, 0, 0};
+            for (int ch = p + 1; ch < pin.z; ch = t.info[ch].z) {
+                const double* cm = t.mom + (size_t)ch * kMom;
+                double s0 = __ldcg(cm + MS0);
+                S += s0;
+                MM_ += __ldcg(cm + MM);
+                for (int a = 0; a < 3; ++a) ww[a] += s0 * __ldcg(cm + MC + a);
+            }
+            int pd = t.depth_leaf[p] & 255;
+            double pctr[3], ps;
+            box_centre(cb, t.cell[p], pd, pctr, &ps);
+            double pcen[3];
+            for (int a = 0; a < 3; ++a) pcen[a] = S > 0.0 ? ww[a] / S : pctr[a];
+            double PD[3] = {0, 0, 0}, PQ[6] = {0, 0, 0, 0, 0, 0};
+            for (int ch = p + 1; ch < pin.z; ch = t.info[ch].z) {
+                const double* cm = t.mom + (size_t)ch * kMom;
+                double mk = __ldcg(cm + MM);
+                double e[3], dk[3], qk[6];
+                for (int a = 0; a < 3; ++a) {
+                    e[a] = __ldcg(cm + MC + a) - pcen[a];
+                    dk[a] = __ldcg(cm + MD + a);
+                }
+                for (int a = 0; a < 6; ++a) qk[a] = __ldcg(cm + MQ + a);
+                for (int a = 0; a < 3; ++a) PD[a] += dk[a] + mk * e[a];
+                // Q += Q_k + D_k e^T + e D_k^T + M_k e e^T
+                PQ[0] += qk[0] + 2.0 * dk[0] * e[0] + mk * e[0] * e[0];
+                PQ[1] += qk[1] + dk[0] * e[1] + e[0] * dk[1] + mk * e[0] * e[1];
+                PQ[2] += qk[2] + dk[0] * e[2] + e[0] * dk[2] + mk * e[0] * e[2];
+                PQ[3] += qk[3] + 2.0 * dk[1] * e[1] + mk * e[1] * e[1];
+                PQ[4] += qk[4] + dk[1] * e[2] + e[1] * dk[2] + mk * e[1] * e[2];
+                PQ[5] += qk[5] + 2.0 * dk[2] * e[2] + mk * e[2] * e[2];
+            }
+            double* pm = t.mom + (size_t)p * kMom;
+            for (int a = 0; a < 3; ++a) {
+                pm[MC + a] = pcen[a];
+                pm[MD + a] = PD[a];
+            }
+            for (int a = 0; a < 6; ++a) pm[MQ + a] = PQ[a];
+            pm[MM] = MM_;
+            pm[MS0] = S;
+            finish_box(pm, pctr);
+            cur = p;
+            cnt = pc;
+        }
+    }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- launchers
+size_t scan_partials_words(int n) { return (size_t)((n + kScanTile - 1) / kScanTile) + 1; }
+
+void launch_scan(const int* in, int* out, int n, int* partials, int* total, cudaStream_t s)
+{
+    count_launch(3);
+    int nb = (n + kScanTile - 1) / kScanTile;
+    if (nb < 1) nb = 1;
+    k_scan_reduce<<<nb, kScanThreads, 0, s>>>(in, n, partials);
+    k_scan_partials<<<1, kScanThreads, 0, s>>>(partials, nb, total);
+    k_scan_apply<<<nb, kScanThreads, 0, s>>>(in, out, n, partials);
+}
+
+void launch_bbox(const double* x, const double* y, const double* z, int n, double* partials,
+                 int nblk, Cube* cube, cudaStream_t s)
+{
+    count_launch(2);
+    k_bbox_partial<<<nblk, 256, 0, s>>>(x, y, z, n, partials);
+    k_bbox_final<<<1, 32, 0, s>>>(partials, nblk, cube);
+}
+
+void launch_keys(const double* x, const double* y, const double* z, int n, const Cube* cube,
+                 unsigned long long* key, unsigned int* val, cudaStream_t s)
+{
+    count_launch(1);
+    k_keys<<<(n + 255) / 256, 256, 0, s>>>(x, y, z, n, cube, key, val);
+}
+
+size_t sort_scratch_words(int n)
+{
+    int nb = (n + kSortTile - 1) / kSortTile;
+    return (size_t)kRadix * (size_t)(nb > 0 ? nb : 1);
+}
+
+void launch_sort(unsigned long long* key[2], unsigned int* val[2], int n, SortScratch sc,
+                 const unsigned int* ids_in, cudaStream_t s)
+{
+    count_launch(17);
+    int nb = (n + kSortTile - 1) / kSortTile;
+    int cur = 0;
+    for (int shift = 0; shift < 64; shift += 8) {
+        k_radix_hist<<<nb, kSortThreads, 0, s>>>(key[cur], n, shift, sc.hist);
+        launch_scan((const int*)sc.hist, (int*)sc.hist, kRadix * nb, (int*)sc.hist_part, nullptr,
+                    s);
+        k_radix_scatter<<<nb, kSortThreads, 0, s>>>(key[cur], val[cur], key[cur ^ 1], val[cur ^ 1],
+                                                    n, shift, sc.hist);
+        cur ^= 1;
+    }
+    // eight passes: the result is back in buffer 0
+    k_tiefix<<<(n + 255) / 256, 256, 0, s>>>(key[0], val[0], ids_in, n);
+}
+
+void launch_tiefix(const unsigned long long* key, unsigned int* perm, const unsigned int* ids,
+                   int n, cudaStream_t s)
+{
+    count_launch(1);
+    k_tiefix<<<(n + 255) / 256, 256, 0, s>>>(key, perm, ids, n);
+}
+
+void launch_topology(const unsigned long long* key, int n, int leaf_cap, int* pos_cnt,
+                     int* pos_off, int* scan_part, Tree t, cudaStream_t s)
+{
+    count_launch(2);
+    cudaMemsetAsync(t.maxdepth, 0, sizeof(int), s);
+    k_topo_count<<<(n + 255) / 256, 256, 0, s>>>(key, n, leaf_cap, pos_cnt);
+    launch_scan(pos_cnt, pos_off, n, scan_part, t.nnodes, s);
+    k_topo_emit<<<(n + 255) / 256, 256, 0, s>>>(key, n, leaf_cap, pos_cnt, pos_off, t);
+}
+
+void launch_moments(const double* x, const double* y, const double* z, const int8_t* sp,
+                    const double* qsp, int n, const Cube* cube, Tree t, float4* src32,
+                    int want_f32, cudaStream_t s)
+{
+    count_launch(1);
+    int blocks = (n + 255) / 256;
+    if (blocks > 4 * 152) blocks = 4 * 152;
+    if (blocks < 1) blocks = 1;
+    k_moments<<<blocks, 256, 0, s>>>(x, y, z, sp, qsp, cube, t, src32, want_f32);
+}
+
+}  // namespace ucp

@@ -1,0 +1,118 @@
+// ucp_internal.cuh -- device data layout and kernel entry points shared by the
+// translation units of libucp (TREE method of arXiv 0709.3331, Sec. 3).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+
+namespace ucp {
+
+constexpr int kMaxDepth = 21;        // 21 bits per axis, 63-bit keys
+constexpr int kWarp = 32;
+
+// Kernels launched by this process (read by ucp_stats).
+extern std::atomic<unsigned long long> g_launches;
+inline void count_launch(int k) { g_launches.fetch_add((unsigned long long)k, std::memory_order_relaxed); }
+
+// One FP64 box record, 16 doubles (128 B), read by the FP64 walk.
+// {c.x, c.y, c.z, rcrit2, M, D.x, D.y, D.z, Qxx, Qxy, Qxz, Qyy, Qyz, Qzz, S0, delta}
+// rcrit2 = (s/theta + delta)^2 is filled per walk (it depends on theta).
+constexpr int kMom = 16;
+enum MomIdx { MC = 0, MR2 = 3, MM = 4, MD = 5, MQ = 8, MS0 = 14, MDELTA = 15 };
+
+// One FP32C box record, 5 float4 (80 B):
+//   A = {ch.x, ch.y, ch.z, rcrit2}   ch = fp32(c), cl = fp32(c - ch)
+//   B = {cl.x, cl.y, cl.z, bits(next)}
+//   C = {bits(begin), bits(end or -1 for a twig), M, D.x}
+//   D = {D.y, D.z, Qxx, Qxy}
+//   E = {Qxz, Qyy, Qyz, Qzz}
+constexpr int kF32 = 5;
+
+// Box topology {begin, end, next, parent}; depth and leaf flag separately.
+struct Tree {
+    int cap;                 // box capacity
+    int* nnodes;             // device scalar
+    int* maxdepth;           // device scalar
+    int4* info;              // {begin, end, next, parent}
+    int* depth_leaf;         // depth | leaf << 8
+    unsigned long long* cell;// key prefix of the box at its depth
+    double* mom;             // kMom doubles per box
+    float4* f32;             // kF32 float4 per box
+    int* arrive;             // bottom-up arrival counters (particles)
+};
+
+struct Cube {                // enclosing cube: centre and side
+    double c[3];
+    double L;
+};
+
+// ---- build (ucp_build.cu) ----
+void launch_bbox(const double* x, const double* y, const double* z, int n, double* partials,
+                 int nblk, Cube* cube, cudaStream_t s);
+void launch_keys(const double* x, const double* y, const double* z, int n, const Cube* cube,
+                 unsigned long long* key, unsigned int* val, cudaStream_t s);
+struct SortScratch {
+    unsigned int* hist;      // 256 x nblocks
+    unsigned int* hist_part; // scan partials
+    int nblocks;
+};
+size_t sort_scratch_words(int n);
+void launch_sort(unsigned long long* key[2], unsigned int* val[2], int n, SortScratch sc,
+                 const unsigned int* ids_in, cudaStream_t s);
+void launch_tiefix(const unsigned long long* key, unsigned int* perm, const unsigned int* ids,
+                   int n, cudaStream_t s);
+void launch_topology(const unsigned long long* key, int n, int leaf_cap, int* pos_cnt,
+                     int* pos_off, int* scan_part, Tree t, cudaStream_t s);
+void launch_moments(const double* x, const double* y, const double* z, const int8_t* sp,
+                    const double* qsp, int n, const Cube* cube, Tree t, float4* src32,
+                    int want_f32, cudaStream_t s);
+void launch_scan(const int* in, int* out, int n, int* partials, int* total, cudaStream_t s);
+size_t scan_partials_words(int n);
+
+// ---- walk (ucp_walk.cu) ----
+struct WalkArgs {
+    const double* x; const double* y; const double* z;
+    const int8_t* sp;
+    const double* qsp;      // charge per species (device, 2)
+    const double* msp;      // mass per species (device, 2)
+    const float4* src32;    // FP32C source offsets and charges (key order)
+    Tree t;
+    const int* targets;     // key-order slots of the targets, or NULL = all
+    int ntargets;
+    double eps2;
+    double* ax; double* ay; double* az; double* phi;  // key order; phi may be NULL
+    int* cnt_p2p; int* cnt_m2p;                        // key order
+    int* work;              // dynamic work counter (zeroed before launch)
+    unsigned long long* stats; // {p2p, m2p}
+};
+void launch_mac_prepare(Tree t, const Cube* cube, double theta, int want_f32, cudaStream_t s);
+void launch_walk_fp64(const WalkArgs& a, int nsm, cudaStream_t s);
+void launch_walk_fp32c(const WalkArgs& a, int nsm, cudaStream_t s);
+
+// ---- push and reductions (ucp_push.cu) ----
+void launch_permute(const unsigned int* perm, int n, const double* const* src6, double* const* dst6,
+                    const int8_t* sp_in, int8_t* sp_out, const unsigned int* id_in,
+                    unsigned int* id_out, cudaStream_t s);
+void launch_kick(double* vx, double* vy, double* vz, const double* ax, const double* ay,
+                 const double* az, const int8_t* sp, int species, double h, int n, int times,
+                 cudaStream_t s);
+void launch_drift(double* x, double* y, double* z, const double* vx, const double* vy,
+                  const double* vz, double dt, int n, cudaStream_t s);
+void launch_select(const int8_t* sp, int species, int n, int* flags, int* list, int* scan_part,
+                   int* count, cudaStream_t s);
+void launch_energy(const double* vx, const double* vy, const double* vz, const double* phi,
+                   const int8_t* sp, const double* qsp, const double* msp, int n,
+                   double* partials, int nblk, double* out6, cudaStream_t s);
+void launch_scatter3(const double* ax, const double* ay, const double* az, const unsigned int* id,
+                     int n, double* out, cudaStream_t s);
+void launch_scatter1(const double* a, const unsigned int* id, int n, double* out, cudaStream_t s);
+void launch_scatter_int(const int* a, const unsigned int* id, int n, int* out, cudaStream_t s);
+void launch_deinterleave(const double* aos, int n, double* x, double* y, double* z,
+                         cudaStream_t s);
+void launch_check_state(const double* pos, const double* vel, const int8_t* sp, int n, int* flags,
+                        cudaStream_t s);
+void launch_iota(unsigned int* a, int n, cudaStream_t s);
+
+}  // namespace ucp

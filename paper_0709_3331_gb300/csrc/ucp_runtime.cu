@@ -1,0 +1,713 @@
+// ucp_runtime.cu -- the C ABI of include/ucp.h: context, device memory, and
+// the order of kernels for TREE construction (Sec. 3), the particle-TREE walk
+// and the split-step velocity Verlet push (Sec. 2) of arXiv 0709.3331.
+#include "ucp.h"
+#include "ucp_internal.cuh"
+
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+using namespace ucp;
+
+std::atomic<unsigned long long> ucp::g_launches{0};
+
+struct ucp_ctx {
+    int n = 0, leaf_cap = 1, precision = UCP_FP64;
+    double q[2] = {1, -1}, m[2] = {1, 1};
+    cudaStream_t s = nullptr;
+    int nsm = 152;
+    int device = 0;
+
+    // particle state in key order, two buffer sets (permutation ping-pong)
+    double* st[2][6] = {};   // x y z vx vy vz
+    int8_t* sp[2] = {};
+    unsigned int* id[2] = {};
+    int cur = 0;
+    double *ax = nullptr, *ay = nullptr, *az = nullptr, *phi = nullptr;
+
+    unsigned long long* key[2] = {};
+    unsigned int* val[2] = {};
+    SortScratch sort = {};
+    int* scan_part = nullptr;
+    int* pos_cnt = nullptr;
+    int* pos_off = nullptr;
+    Tree t = {};
+    float4* src32 = nullptr;
+    Cube* cube = nullptr;
+    double* bbox_part = nullptr;
+    int bbox_nblk = 1;
+    double* qsp = nullptr;
+    double* msp = nullptr;
+    int* tflags = nullptr;
+    int* tlist = nullptr;    // 2n: compacted list, then scan offsets
+    int* tcount = nullptr;
+    int* cnt_p2p = nullptr;
+    int* cnt_m2p = nullptr;
+    int* work = nullptr;
+    unsigned long long* stats = nullptr;  // {p2p, m2p}
+    double* en_part = nullptr;
+    int en_nblk = 1;
+    double* en_out = nullptr;
+    int* flags = nullptr;
+    double* stage = nullptr;  // n x 6 doubles for host transfers and layout changes
+    int8_t* stage_sp = nullptr;
+    int* stage_int = nullptr;
+
+    int n_e = 0;
+    bool have_state = false, tree_valid = false, acc_valid = false;
+    bool phi_valid = false;           // phi of every particle at the current positions
+    double phi_theta = -1.0, phi_eps = -1.0;
+    int64_t steps = 0, walk_targets = 0, walk_launches = 0;
+    unsigned long long launch_base = 0;
+
+    bool prof = false;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
+    size_t ev_used = 0;
+    double prof_ms = 0.0;
+    int64_t prof_launches = 0;
+
+    std::string err;
+    std::vector<void*> allocs;
+};
+
+namespace {
+
+int fail(ucp_ctx* c, int code, const std::string& msg)
+{
+    if (c) c->err = msg;
+    return code;
+}
+
+#define CK(call)                                                                      \
+    do {                                                                              \
+        cudaError_t e_ = (call);                                                      \
+        if (e_ != cudaSuccess)                                                        \
+            return fail(c, UCP_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+int check_launch(ucp_ctx* c, const char* where)
+{
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(c, UCP_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+    return UCP_OK;
+}
+
+template <class T>
+int dalloc(ucp_ctx* c, T** p, size_t count)
+{
+    void* q = nullptr;
+    cudaError_t e = cudaMalloc(&q, (count ? count : 1) * sizeof(T));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, UCP_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    }
+    c->allocs.push_back(q);
+    *p = (T*)q;
+    return UCP_OK;
+}
+
+// Upper bound on the number of boxes: depth d holds at most 8^d boxes, at most
+// n, and at most 8 per twig of depth d-1, of which there are <= n/(leaf_cap+1).
+int64_t box_capacity(int64_t n, int leaf_cap)
+{
+    int64_t twigs = n / (leaf_cap + 1);
+    int64_t total = 0, pow8 = 1;
+    for (int d = 0; d <= kMaxDepth; ++d) {
+        int64_t lim = n;
+        if (d > 0 && 8 * twigs < lim) lim = 8 * twigs;
+        if (pow8 < lim) lim = pow8;
+        total += lim;
+        if (pow8 < ((int64_t)1 << 40)) pow8 *= 8;
+    }
+    return total < 1 ? 1 : total;
+}
+
+void prof_begin(ucp_ctx* c)
+{
+    if (!c->prof) return;
+    if (c->ev_used == c->ev.size()) {
+        cudaEvent_t a, b;
+        cudaEventCreate(&a);
+        cudaEventCreate(&b);
+        c->ev.push_back({a, b});
+    }
+    cudaEventRecord(c->ev[c->ev_used].first, c->s);
+}
+
+void prof_end(ucp_ctx* c)
+{
+    if (!c->prof) return;
+    cudaEventRecord(c->ev[c->ev_used].second, c->s);
+    ++c->ev_used;
+}
+
+// Sec. 3 construction: cube, keys, sort, permutation of the state, boxes, moments.
+int build(ucp_ctx* c)
+{
+    int n = c->n, k = c->cur;
+    launch_bbox(c->st[k][0], c->st[k][1], c->st[k][2], n, c->bbox_part, c->bbox_nblk, c->cube,
+                c->s);
+    launch_keys(c->st[k][0], c->st[k][1], c->st[k][2], n, c->cube, c->key[0], c->val[0], c->s);
+    launch_sort(c->key, c->val, n, c->sort, c->id[k], c->s);
+    const double* src[6];
+    double* dst[6];
+    for (int a = 0; a < 6; ++a) {
+        src[a] = c->st[k][a];
+        dst[a] = c->st[k ^ 1][a];
+    }
+    launch_permute(c->val[0], n, src, dst, c->sp[k], c->sp[k ^ 1], c->id[k], c->id[k ^ 1], c->s);
+    c->cur = k ^ 1;
+    k = c->cur;
+    launch_topology(c->key[0], n, c->leaf_cap, c->pos_cnt, c->pos_off, c->scan_part, c->t, c->s);
+    launch_moments(c->st[k][0], c->st[k][1], c->st[k][2], c->sp[k], c->qsp, n, c->cube, c->t,
+                   c->src32, c->precision == UCP_FP32C, c->s);
+    c->tree_valid = true;
+    c->acc_valid = false;
+    c->phi_valid = false;
+    return check_launch(c, "tree build");
+}
+
+// One walk over all particles (electrons_only = 0) or the electrons.
+int force(ucp_ctx* c, double theta, double eps, int electrons_only, bool want_phi)
+{
+    int k = c->cur;
+    int f32 = c->precision == UCP_FP32C;
+    launch_mac_prepare(c->t, c->cube, theta, f32, c->s);
+    WalkArgs a;
+    a.x = c->st[k][0];
+    a.y = c->st[k][1];
+    a.z = c->st[k][2];
+    a.sp = c->sp[k];
+    a.qsp = c->qsp;
+    a.msp = c->msp;
+    a.src32 = c->src32;
+    a.t = c->t;
+    if (electrons_only) {
+        launch_select(c->sp[k], UCP_ELECTRON, c->n, c->tflags, c->tlist, c->scan_part, c->tcount,
+                      c->s);
+        a.targets = c->tlist;
+        a.ntargets = c->n_e;
+    } else {
+        a.targets = nullptr;
+        a.ntargets = c->n;
+    }
+    a.eps2 = eps * eps;
+    a.ax = c->ax;
+    a.ay = c->ay;
+    a.az = c->az;
+    a.phi = want_phi ? c->phi : nullptr;
+    a.cnt_p2p = c->cnt_p2p;
+    a.cnt_m2p = c->cnt_m2p;
+    a.work = c->work;
+    a.stats = c->stats;
+    cudaMemsetAsync(c->cnt_p2p, 0, sizeof(int) * (size_t)c->n, c->s);
+    cudaMemsetAsync(c->cnt_m2p, 0, sizeof(int) * (size_t)c->n, c->s);
+    if (a.ntargets > 0) {
+        prof_begin(c);
+        if (f32) launch_walk_fp32c(a, c->nsm, c->s);
+        else launch_walk_fp64(a, c->nsm, c->s);
+        prof_end(c);
+        c->walk_targets += a.ntargets;
+        c->walk_launches += 1;
+    }
+    if (!electrons_only) c->acc_valid = true;
+    if (!electrons_only && want_phi) {
+        c->phi_valid = true;
+        c->phi_theta = theta;
+        c->phi_eps = eps;
+    }
+    return check_launch(c, "tree walk");
+}
+
+int valid_walk_args(ucp_ctx* c, double theta, double eps)
+{
+    if (!(theta >= 0.0 && theta <= 1.0)) return fail(c, UCP_EINVAL, "theta must be in [0, 1]");
+    if (!(eps >= 0.0) || !std::isfinite(eps)) return fail(c, UCP_EINVAL, "eps must be >= 0");
+    return UCP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* ucp_strerror(int code)
+{
+    switch (code) {
+    case UCP_OK: return "ok";
+    case UCP_EINVAL: return "invalid argument";
+    case UCP_ENOMEM: return "out of memory";
+    case UCP_ECUDA: return "CUDA error";
+    case UCP_ENONFINITE: return "non-finite position or velocity";
+    case UCP_ETIMEOUT: return "device wait timed out";
+    case UCP_ESTATE: return "no particle state set";
+    default: return "unknown error";
+    }
+}
+
+const char* ucp_last_error(ucp_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+void ucp_destroy(ucp_ctx* c)
+{
+    if (!c) return;
+    if (c->s) cudaStreamSynchronize(c->s);
+    else cudaDeviceSynchronize();
+    for (void* p : c->allocs) cudaFree(p);
+    for (auto& e : c->ev) {
+        cudaEventDestroy(e.first);
+        cudaEventDestroy(e.second);
+    }
+    delete c;
+}
+
+int ucp_create(ucp_ctx** out, const ucp_params* p)
+{
+    if (!out || !p) return UCP_EINVAL;
+    *out = nullptr;
+    if (p->n < 1 || p->n > 0x7fffffffLL) return UCP_EINVAL;
+    if (p->leaf_cap < 1 || p->leaf_cap > 1024) return UCP_EINVAL;
+    if (p->precision != UCP_FP64 && p->precision != UCP_FP32C) return UCP_EINVAL;
+    for (int s = 0; s < 2; ++s)
+        if (!(p->m[s] > 0.0) || !std::isfinite(p->m[s]) || !std::isfinite(p->q[s]))
+            return UCP_EINVAL;
+    int64_t cap = box_capacity(p->n, p->leaf_cap);
+    if (cap > 0x7ffffff0LL) return UCP_EINVAL;
+
+    ucp_ctx* c = new (std::nothrow) ucp_ctx();
+    if (!c) return UCP_ENOMEM;
+    c->n = (int)p->n;
+    c->leaf_cap = p->leaf_cap;
+    c->precision = p->precision;
+    for (int s = 0; s < 2; ++s) {
+        c->q[s] = p->q[s];
+        c->m[s] = p->m[s];
+    }
+    c->s = (cudaStream_t)p->cuda_stream;
+    int rc = UCP_OK;
+    auto bail = [&](int code) {
+        std::string msg = c->err;
+        ucp_destroy(c);
+        return code;
+    };
+    if (cudaGetDevice(&c->device) != cudaSuccess) return bail(UCP_ECUDA);
+    cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, c->device);
+    size_t n = (size_t)c->n;
+    for (int b = 0; b < 2; ++b) {
+        for (int a = 0; a < 6; ++a)
+            if ((rc = dalloc(c, &c->st[b][a], n))) return bail(rc);
+        if ((rc = dalloc(c, &c->sp[b], n))) return bail(rc);
+        if ((rc = dalloc(c, &c->id[b], n))) return bail(rc);
+        if ((rc = dalloc(c, &c->key[b], n))) return bail(rc);
+        if ((rc = dalloc(c, &c->val[b], n))) return bail(rc);
+    }
+    if ((rc = dalloc(c, &c->ax, n)) || (rc = dalloc(c, &c->ay, n)) || (rc = dalloc(c, &c->az, n)) ||
+        (rc = dalloc(c, &c->phi, n)))
+        return bail(rc);
+    size_t sw = sort_scratch_words(c->n);
+    c->sort.nblocks = (int)(sw / 256);
+    if ((rc = dalloc(c, &c->sort.hist, sw)) ||
+        (rc = dalloc(c, &c->sort.hist_part, scan_partials_words((int)sw))))
+        return bail(rc);
+    size_t spw = scan_partials_words(c->n);
+    if (spw < scan_partials_words((int)sw)) spw = scan_partials_words((int)sw);
+    if ((rc = dalloc(c, &c->scan_part, spw))) return bail(rc);
+    if ((rc = dalloc(c, &c->pos_cnt, n)) || (rc = dalloc(c, &c->pos_off, n))) return bail(rc);
+    c->t.cap = (int)cap;
+    size_t cz = (size_t)cap;
+    if ((rc = dalloc(c, &c->t.nnodes, 1)) || (rc = dalloc(c, &c->t.maxdepth, 1)) ||
+        (rc = dalloc(c, &c->t.info, cz)) || (rc = dalloc(c, &c->t.depth_leaf, cz)) ||
+        (rc = dalloc(c, &c->t.cell, cz)) || (rc = dalloc(c, &c->t.mom, cz * kMom)) ||
+        (rc = dalloc(c, &c->t.arrive, cz)))
+        return bail(rc);
+    if (c->precision == UCP_FP32C) {
+        if ((rc = dalloc(c, &c->t.f32, cz * kF32)) || (rc = dalloc(c, &c->src32, n)))
+            return bail(rc);
+    }
+    if ((rc = dalloc(c, &c->cube, 1))) return bail(rc);
+    c->bbox_nblk = (int)((n + 2047) / 2048);
+    if (c->bbox_nblk > 4 * c->nsm) c->bbox_nblk = 4 * c->nsm;
+    if (c->bbox_nblk < 1) c->bbox_nblk = 1;
+    c->en_nblk = c->bbox_nblk;
+    if ((rc = dalloc(c, &c->bbox_part, (size_t)c->bbox_nblk * 6)) ||
+        (rc = dalloc(c, &c->en_part, (size_t)c->en_nblk * 6)) || (rc = dalloc(c, &c->en_out, 6)))
+        return bail(rc);
+    if ((rc = dalloc(c, &c->qsp, 2)) || (rc = dalloc(c, &c->msp, 2))) return bail(rc);
+    if ((rc = dalloc(c, &c->tflags, n)) || (rc = dalloc(c, &c->tlist, 2 * n)) ||
+        (rc = dalloc(c, &c->tcount, 1)))
+        return bail(rc);
+    if ((rc = dalloc(c, &c->cnt_p2p, n)) || (rc = dalloc(c, &c->cnt_m2p, n)) ||
+        (rc = dalloc(c, &c->work, 1)) || (rc = dalloc(c, &c->stats, 2)) ||
+        (rc = dalloc(c, &c->flags, 2)))
+        return bail(rc);
+    if ((rc = dalloc(c, &c->stage, 6 * n)) || (rc = dalloc(c, &c->stage_sp, n)) ||
+        (rc = dalloc(c, &c->stage_int, 2 * n)))
+        return bail(rc);
+    if (cudaMemcpyAsync(c->qsp, c->q, 2 * sizeof(double), cudaMemcpyHostToDevice, c->s) ||
+        cudaMemcpyAsync(c->msp, c->m, 2 * sizeof(double), cudaMemcpyHostToDevice, c->s) ||
+        cudaMemsetAsync(c->stats, 0, 2 * sizeof(unsigned long long), c->s) ||
+        cudaStreamSynchronize(c->s)) {
+        c->err = "initial copies failed";
+        return bail(UCP_ECUDA);
+    }
+    *out = c;
+    return UCP_OK;
+}
+
+int ucp_set_state(ucp_ctx* c, const double* pos, const double* vel, const int8_t* species,
+                  int on_device)
+{
+    if (!c) return UCP_EINVAL;
+    if (!pos || !vel || !species) return fail(c, UCP_EINVAL, "null pointer");
+    size_t n = (size_t)c->n;
+    const double* dpos = pos;
+    const double* dvel = vel;
+    const int8_t* dsp = species;
+    int k = c->cur;
+    if (!on_device) {
+        int ne = 0;
+        for (size_t i = 0; i < n; ++i) {
+            for (int a = 0; a < 3; ++a)
+                if (!std::isfinite(pos[3 * i + a]) || !std::isfinite(vel[3 * i + a]))
+                    return fail(c, UCP_ENONFINITE, "non-finite position or velocity");
+            if (species[i] != 0 && species[i] != 1)
+                return fail(c, UCP_EINVAL, "species must be 0 (ion) or 1 (electron)");
+            ne += species[i] == 1;
+        }
+        CK(cudaMemcpyAsync(c->stage, pos, 3 * n * sizeof(double), cudaMemcpyHostToDevice, c->s));
+        CK(cudaMemcpyAsync(c->stage + 3 * n, vel, 3 * n * sizeof(double), cudaMemcpyHostToDevice,
+                           c->s));
+        CK(cudaMemcpyAsync(c->sp[k], species, n, cudaMemcpyHostToDevice, c->s));
+        dpos = c->stage;
+        dvel = c->stage + 3 * n;
+        c->n_e = ne;
+    } else {
+        CK(cudaMemsetAsync(c->flags, 0, 2 * sizeof(int), c->s));
+        launch_check_state(pos, vel, species, c->n, c->flags, c->s);
+        int fl[2] = {0, 0};
+        CK(cudaMemcpyAsync(fl, c->flags, sizeof(fl), cudaMemcpyDeviceToHost, c->s));
+        CK(cudaStreamSynchronize(c->s));
+        if (fl[0]) return fail(c, UCP_ENONFINITE, "non-finite position or velocity");
+        if (fl[1]) return fail(c, UCP_EINVAL, "species must be 0 (ion) or 1 (electron)");
+        CK(cudaMemcpyAsync(c->sp[k], dsp, n, cudaMemcpyDeviceToDevice, c->s));
+        launch_select(c->sp[k], UCP_ELECTRON, c->n, c->tflags, c->tlist, c->scan_part, c->tcount,
+                      c->s);
+        int ne = 0;
+        CK(cudaMemcpyAsync(&ne, c->tcount, sizeof(int), cudaMemcpyDeviceToHost, c->s));
+        CK(cudaStreamSynchronize(c->s));
+        c->n_e = ne;
+    }
+    launch_deinterleave(dpos, c->n, c->st[k][0], c->st[k][1], c->st[k][2], c->s);
+    launch_deinterleave(dvel, c->n, c->st[k][3], c->st[k][4], c->st[k][5], c->s);
+    launch_iota(c->id[k], c->n, c->s);
+    c->have_state = true;
+    c->tree_valid = false;
+    c->acc_valid = false;
+    c->phi_valid = false;
+    c->steps = 0;
+    int rc = check_launch(c, "set_state");
+    if (rc) return rc;
+    if (!on_device) CK(cudaStreamSynchronize(c->s));
+    return UCP_OK;
+}
+
+int ucp_get_state(ucp_ctx* c, double* pos, double* vel, int on_device)
+{
+    if (!c) return UCP_EINVAL;
+    if (!c->have_state) return fail(c, UCP_ESTATE, "no state");
+    size_t n = (size_t)c->n;
+    int k = c->cur;
+    double* outs[2] = {pos, vel};
+    for (int w = 0; w < 2; ++w) {
+        if (!outs[w]) continue;
+        double* dst = on_device ? outs[w] : c->stage + 3 * n * w;
+        launch_scatter3(c->st[k][3 * w], c->st[k][3 * w + 1], c->st[k][3 * w + 2], c->id[k],
+                        c->n, dst, c->s);
+        if (!on_device)
+            CK(cudaMemcpyAsync(outs[w], dst, 3 * n * sizeof(double), cudaMemcpyDeviceToHost,
+                               c->s));
+    }
+    int rc = check_launch(c, "get_state");
+    if (rc) return rc;
+    if (!on_device) CK(cudaStreamSynchronize(c->s));
+    return UCP_OK;
+}
+
+int ucp_tree_build(ucp_ctx* c)
+{
+    if (!c) return UCP_EINVAL;
+    if (!c->have_state) return fail(c, UCP_ESTATE, "no state");
+    if (c->tree_valid) return UCP_OK;
+    return build(c);
+}
+
+int ucp_tree_force(ucp_ctx* c, double theta, double eps, double* acc, double* phi, int on_device)
+{
+    if (!c) return UCP_EINVAL;
+    if (!c->have_state) return fail(c, UCP_ESTATE, "no state");
+    int rc = valid_walk_args(c, theta, eps);
+    if (rc) return rc;
+    if (!c->tree_valid && (rc = build(c))) return rc;
+    if ((rc = force(c, theta, eps, 0, phi != nullptr))) return rc;
+    size_t n = (size_t)c->n;
+    int k = c->cur;
+    if (acc) {
+        double* dst = on_device ? acc : c->stage;
+        launch_scatter3(c->ax, c->ay, c->az, c->id[k], c->n, dst, c->s);
+        if (!on_device)
+            CK(cudaMemcpyAsync(acc, dst, 3 * n * sizeof(double), cudaMemcpyDeviceToHost, c->s));
+    }
+    if (phi) {
+        double* dst = on_device ? phi : c->stage + 3 * n;
+        launch_scatter1(c->phi, c->id[k], c->n, dst, c->s);
+        if (!on_device)
+            CK(cudaMemcpyAsync(phi, dst, n * sizeof(double), cudaMemcpyDeviceToHost, c->s));
+    }
+    if ((rc = check_launch(c, "tree_force"))) return rc;
+    if (!on_device) CK(cudaStreamSynchronize(c->s));
+    return UCP_OK;
+}
+
+int ucp_step(ucp_ctx* c, double dt_e, int kk, int64_t n_electron_steps, double theta, double eps)
+{
+    if (!c) return UCP_EINVAL;
+    if (!c->have_state) return fail(c, UCP_ESTATE, "no state");
+    if (!(dt_e > 0.0) || !std::isfinite(dt_e)) return fail(c, UCP_EINVAL, "dt_e must be > 0");
+    if (kk < 1) return fail(c, UCP_EINVAL, "ion_substep_ratio must be >= 1");
+    if (n_electron_steps < 0 || n_electron_steps % kk)
+        return fail(c, UCP_EINVAL, "n_electron_steps must be a non-negative multiple of k");
+    int rc = valid_walk_args(c, theta, eps);
+    if (rc) return rc;
+    if (!c->acc_valid) {
+        if (!c->tree_valid && (rc = build(c))) return rc;
+        if ((rc = force(c, theta, eps, 0, false))) return rc;
+    }
+    const double dt_i = (double)kk * dt_e;
+    const double h_i = 0.5 * dt_i, h_e = 0.5 * dt_e;
+    int64_t nblocks = n_electron_steps / kk;
+    int pend_i = 0, pend_e = 0;
+    for (int64_t b = 0; b < nblocks; ++b) {
+        int k = c->cur;
+        launch_kick(c->st[k][3], c->st[k][4], c->st[k][5], c->ax, c->ay, c->az, c->sp[k], UCP_ION,
+                    h_i, c->n, 1 + pend_i, c->s);
+        pend_i = 0;
+        for (int sub = 1; sub <= kk; ++sub) {
+            k = c->cur;
+            launch_kick(c->st[k][3], c->st[k][4], c->st[k][5], c->ax, c->ay, c->az, c->sp[k],
+                        UCP_ELECTRON, h_e, c->n, 1 + pend_e, c->s);
+            pend_e = 0;
+            launch_drift(c->st[k][0], c->st[k][1], c->st[k][2], c->st[k][3], c->st[k][4],
+                         c->st[k][5], dt_e, c->n, c->s);
+            if ((rc = build(c))) return rc;
+            // the walk over every particle also leaves phi for a following ucp_energy
+            if ((rc = force(c, theta, eps, sub < kk, sub == kk))) return rc;
+            pend_e = 1;
+        }
+        pend_i = 1;
+        c->steps += kk;
+    }
+    int k = c->cur;
+    if (pend_e)
+        launch_kick(c->st[k][3], c->st[k][4], c->st[k][5], c->ax, c->ay, c->az, c->sp[k],
+                    UCP_ELECTRON, h_e, c->n, 1, c->s);
+    if (pend_i)
+        launch_kick(c->st[k][3], c->st[k][4], c->st[k][5], c->ax, c->ay, c->az, c->sp[k], UCP_ION,
+                    h_i, c->n, 1, c->s);
+    return check_launch(c, "step");
+}
+
+int ucp_energy(ucp_ctx* c, double theta, double eps, double out[6])
+{
+    if (!c || !out) return UCP_EINVAL;
+    if (!c->have_state) return fail(c, UCP_ESTATE, "no state");
+    int rc = valid_walk_args(c, theta, eps);
+    if (rc) return rc;
+    if (!c->tree_valid && (rc = build(c))) return rc;
+    if (!(c->phi_valid && c->phi_theta == theta && c->phi_eps == eps) &&
+        (rc = force(c, theta, eps, 0, true)))
+        return rc;
+    int k = c->cur;
+    launch_energy(c->st[k][3], c->st[k][4], c->st[k][5], c->phi, c->sp[k], c->qsp, c->msp, c->n,
+                  c->en_part, c->en_nblk, c->en_out, c->s);
+    double r[6];
+    CK(cudaMemcpyAsync(r, c->en_out, sizeof(r), cudaMemcpyDeviceToHost, c->s));
+    CK(cudaStreamSynchronize(c->s));
+    if ((rc = check_launch(c, "energy"))) return rc;
+    out[0] = r[0];
+    out[1] = r[1];
+    out[2] = r[2];
+    out[3] = r[0] + r[1] + r[2];
+    out[4] = std::sqrt(r[3] * r[3] + r[4] * r[4] + r[5] * r[5]);
+    out[5] = (double)c->steps;
+    return UCP_OK;
+}
+
+int ucp_stats(ucp_ctx* c, int64_t out[8], int reset)
+{
+    if (!c || !out) return UCP_EINVAL;
+    unsigned long long s2[2] = {0, 0};
+    int nn = 0, md = 0;
+    CK(cudaMemcpyAsync(s2, c->stats, sizeof(s2), cudaMemcpyDeviceToHost, c->s));
+    if (c->tree_valid) {
+        CK(cudaMemcpyAsync(&nn, c->t.nnodes, sizeof(int), cudaMemcpyDeviceToHost, c->s));
+        CK(cudaMemcpyAsync(&md, c->t.maxdepth, sizeof(int), cudaMemcpyDeviceToHost, c->s));
+    }
+    CK(cudaStreamSynchronize(c->s));
+    out[0] = (int64_t)s2[0];
+    out[1] = (int64_t)s2[1];
+    out[2] = c->walk_targets;
+    out[3] = c->walk_launches;
+    out[4] = nn;
+    out[5] = md;
+    unsigned long long gl = g_launches.load();
+    out[6] = (int64_t)(gl - c->launch_base);
+    out[7] = 0;
+    if (reset) {
+        c->launch_base = gl;
+        CK(cudaMemsetAsync(c->stats, 0, sizeof(s2), c->s));
+        CK(cudaStreamSynchronize(c->s));
+        c->walk_targets = 0;
+        c->walk_launches = 0;
+    }
+    return UCP_OK;
+}
+
+int ucp_get_cube(ucp_ctx* c, double out[4])
+{
+    if (!c || !out) return UCP_EINVAL;
+    if (!c->tree_valid) return fail(c, UCP_ESTATE, "no tree built");
+    Cube cb;
+    CK(cudaMemcpyAsync(&cb, c->cube, sizeof(cb), cudaMemcpyDeviceToHost, c->s));
+    CK(cudaStreamSynchronize(c->s));
+    out[0] = cb.c[0];
+    out[1] = cb.c[1];
+    out[2] = cb.c[2];
+    out[3] = cb.L;
+    return UCP_OK;
+}
+
+int ucp_get_sorted(ucp_ctx* c, uint64_t* keys, uint32_t* ids, int on_device)
+{
+    if (!c) return UCP_EINVAL;
+    if (!c->tree_valid) return fail(c, UCP_ESTATE, "no tree built");
+    size_t n = (size_t)c->n;
+    cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (keys) CK(cudaMemcpyAsync(keys, c->key[0], n * 8, kind, c->s));
+    if (ids) CK(cudaMemcpyAsync(ids, c->id[c->cur], n * 4, kind, c->s));
+    if (!on_device) CK(cudaStreamSynchronize(c->s));
+    return UCP_OK;
+}
+
+static unsigned int host_compact3(unsigned long long x)
+{
+    unsigned int r = 0;
+    for (int b = 0; b < 21; ++b) r |= (unsigned int)((x >> (3 * b)) & 1ull) << b;
+    return r;
+}
+
+int ucp_get_tree(ucp_ctx* c, int64_t* nnodes, int64_t cap, int32_t* topo, int8_t* is_leaf,
+                 double* geom)
+{
+    if (!c || !nnodes) return UCP_EINVAL;
+    if (!c->tree_valid) return fail(c, UCP_ESTATE, "no tree built");
+    int nn = 0;
+    Cube cb;
+    CK(cudaMemcpyAsync(&nn, c->t.nnodes, sizeof(int), cudaMemcpyDeviceToHost, c->s));
+    CK(cudaMemcpyAsync(&cb, c->cube, sizeof(cb), cudaMemcpyDeviceToHost, c->s));
+    CK(cudaStreamSynchronize(c->s));
+    *nnodes = nn;
+    if (!topo && !is_leaf && !geom) return UCP_OK;
+    if (cap < nn) return fail(c, UCP_EINVAL, "capacity smaller than the box count");
+    std::vector<int4> info(nn);
+    std::vector<int> dl(nn);
+    std::vector<unsigned long long> cell(nn);
+    std::vector<double> mom((size_t)nn * kMom);
+    CK(cudaMemcpyAsync(info.data(), c->t.info, sizeof(int4) * nn, cudaMemcpyDeviceToHost, c->s));
+    CK(cudaMemcpyAsync(dl.data(), c->t.depth_leaf, sizeof(int) * nn, cudaMemcpyDeviceToHost, c->s));
+    CK(cudaMemcpyAsync(cell.data(), c->t.cell, 8 * (size_t)nn, cudaMemcpyDeviceToHost, c->s));
+    CK(cudaMemcpyAsync(mom.data(), c->t.mom, sizeof(double) * kMom * nn, cudaMemcpyDeviceToHost,
+                       c->s));
+    CK(cudaStreamSynchronize(c->s));
+    for (int i = 0; i < nn; ++i) {
+        int d = dl[i] & 255;
+        if (topo) {
+            topo[4 * i] = info[i].x;
+            topo[4 * i + 1] = info[i].y;
+            topo[4 * i + 2] = info[i].z;
+            topo[4 * i + 3] = d;
+        }
+        if (is_leaf) is_leaf[i] = (dl[i] & 256) ? 1 : 0;
+        if (geom) {
+            double* g = geom + 20 * (size_t)i;
+            double s = std::ldexp(cb.L, -d);
+            unsigned int ic[3] = {host_compact3(cell[i]), host_compact3(cell[i] >> 1),
+                                  host_compact3(cell[i] >> 2)};
+            for (int a = 0; a < 3; ++a) {
+                volatile double lo = cb.c[a] - cb.L * 0.5;
+                volatile double off = ((double)ic[a] + 0.5) * s;
+                g[a] = lo + off;
+            }
+            g[3] = s;
+            const double* m = mom.data() + (size_t)i * kMom;
+            g[4] = m[MS0];
+            g[5] = m[MM];
+            for (int a = 0; a < 3; ++a) g[6 + a] = m[MC + a];
+            for (int a = 0; a < 3; ++a) g[9 + a] = m[MD + a];
+            for (int a = 0; a < 6; ++a) g[12 + a] = m[MQ + a];
+            g[18] = m[MDELTA];
+            g[19] = 0.0;
+        }
+    }
+    return UCP_OK;
+}
+
+int ucp_get_counts(ucp_ctx* c, int32_t* p2p, int32_t* m2p, int on_device)
+{
+    if (!c) return UCP_EINVAL;
+    if (!c->have_state) return fail(c, UCP_ESTATE, "no state");
+    size_t n = (size_t)c->n;
+    int k = c->cur;
+    int32_t* outs[2] = {p2p, m2p};
+    const int* srcs[2] = {c->cnt_p2p, c->cnt_m2p};
+    for (int w = 0; w < 2; ++w) {
+        if (!outs[w]) continue;
+        int* dst = on_device ? outs[w] : c->stage_int + n * w;
+        launch_scatter_int(srcs[w], c->id[k], c->n, dst, c->s);
+        if (!on_device)
+            CK(cudaMemcpyAsync(outs[w], dst, n * 4, cudaMemcpyDeviceToHost, c->s));
+    }
+    int rc = check_launch(c, "get_counts");
+    if (rc) return rc;
+    if (!on_device) CK(cudaStreamSynchronize(c->s));
+    return UCP_OK;
+}
+
+int ucp_profile(ucp_ctx* c, int enable)
+{
+    if (!c) return UCP_EINVAL;
+    c->prof = enable != 0;
+    return UCP_OK;
+}
+
+int ucp_profile_read(ucp_ctx* c, double* walk_ms, int64_t* launches)
+{
+    if (!c) return UCP_EINVAL;
+    CK(cudaStreamSynchronize(c->s));
+    double tot = 0.0;
+    for (size_t i = 0; i < c->ev_used; ++i) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, c->ev[i].first, c->ev[i].second));
+        tot += ms;
+    }
+    if (walk_ms) *walk_ms = tot;
+    if (launches) *launches = (int64_t)c->ev_used;
+    c->ev_used = 0;
+    return UCP_OK;
+}
+
+}  // extern "C"

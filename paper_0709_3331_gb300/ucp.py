@@ -1,0 +1,235 @@
+"""Python binding of the C ABI in ``include/ucp.h`` (``libucp.so``).
+
+Argument marshalling only: every step of the TREE path runs in the CUDA
+kernels of the library.  Arrays may be numpy arrays (host) or torch CUDA
+tensors (device, used in the order of the context's stream).  If the library
+has not been built the import of :func:`lib` raises: there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libucp.so")
+
+UCP_OK, UCP_EINVAL, UCP_ENOMEM, UCP_ECUDA, UCP_ENONFINITE, UCP_ETIMEOUT, UCP_ESTATE = (
+    0, -1, -2, -3, -4, -5, -6)
+UCP_FP64, UCP_FP32C = 0, 1
+UCP_ION, UCP_ELECTRON = 0, 1
+
+EXPORTS = ("ucp_create", "ucp_destroy", "ucp_set_state", "ucp_get_state", "ucp_tree_build",
+           "ucp_tree_force", "ucp_step", "ucp_energy", "ucp_stats", "ucp_get_cube",
+           "ucp_get_sorted", "ucp_get_tree", "ucp_get_counts", "ucp_profile", "ucp_profile_read",
+           "ucp_strerror", "ucp_last_error")
+
+
+class UcpError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{msg} (code {code})")
+        self.code = code
+
+
+class ucp_params(C.Structure):
+    _fields_ = [("n", C.c_int64), ("leaf_cap", C.c_int32), ("precision", C.c_int32),
+                ("q", C.c_double * 2), ("m", C.c_double * 2), ("cuda_stream", C.c_void_p)]
+
+
+_lib = None
+
+
+def lib():
+    """Load ``libucp.so`` (raises if it was not built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with __graft_entry__.build()")
+        L = C.CDLL(LIB_PATH)
+        vp, i32, i64, dbl = C.c_void_p, C.c_int, C.c_int64, C.c_double
+        L.ucp_create.argtypes = [C.POINTER(vp), C.POINTER(ucp_params)]
+        L.ucp_destroy.argtypes = [vp]
+        L.ucp_destroy.restype = None
+        L.ucp_set_state.argtypes = [vp, vp, vp, vp, i32]
+        L.ucp_get_state.argtypes = [vp, vp, vp, i32]
+        L.ucp_tree_build.argtypes = [vp]
+        L.ucp_tree_force.argtypes = [vp, dbl, dbl, vp, vp, i32]
+        L.ucp_step.argtypes = [vp, dbl, i32, i64, dbl, dbl]
+        L.ucp_energy.argtypes = [vp, dbl, dbl, vp]
+        L.ucp_stats.argtypes = [vp, vp, i32]
+        L.ucp_get_cube.argtypes = [vp, vp]
+        L.ucp_get_sorted.argtypes = [vp, vp, vp, i32]
+        L.ucp_get_tree.argtypes = [vp, C.POINTER(i64), i64, vp, vp, vp]
+        L.ucp_get_counts.argtypes = [vp, vp, vp, i32]
+        L.ucp_profile.argtypes = [vp, i32]
+        L.ucp_profile_read.argtypes = [vp, C.POINTER(dbl), C.POINTER(i64)]
+        L.ucp_strerror.argtypes = [i32]
+        L.ucp_strerror.restype = C.c_char_p
+        L.ucp_last_error.argtypes = [vp]
+        L.ucp_last_error.restype = C.c_char_p
+        for name in ("ucp_create", "ucp_set_state", "ucp_get_state", "ucp_tree_build",
+                     "ucp_tree_force", "ucp_step", "ucp_energy", "ucp_stats", "ucp_get_cube",
+                     "ucp_get_sorted", "ucp_get_tree", "ucp_get_counts", "ucp_profile",
+                     "ucp_profile_read"):
+            getattr(L, name).restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def _is_torch(a):
+    return type(a).__module__.startswith("torch")
+
+
+def _ptr(a, dtype):
+    """(pointer, on_device) of a numpy array or torch tensor of the given dtype."""
+    if a is None:
+        return None, 0
+    if _is_torch(a):
+        import torch
+        tdt = {np.float64: torch.float64, np.int8: torch.int8, np.int32: torch.int32,
+               np.uint64: torch.uint64, np.uint32: torch.uint32}[dtype]
+        if a.dtype != tdt or not a.is_contiguous():
+            raise TypeError(f"tensor must be contiguous {tdt}")
+        return a.data_ptr(), 1 if a.is_cuda else 0
+    if not isinstance(a, np.ndarray) or a.dtype != dtype or not a.flags.c_contiguous:
+        raise TypeError(f"array must be a C-contiguous numpy {np.dtype(dtype)}")
+    return a.ctypes.data, 0
+
+
+class Context:
+    """One particle set on the current CUDA device (``ucp_create`` .. ``ucp_destroy``)."""
+
+    def __init__(self, n, q=(1.0, -1.0), m=(1000.0, 1.0), leaf_cap=16, precision=UCP_FP64,
+                 stream=None):
+        L = lib()
+        p = ucp_params()
+        p.n = int(n)
+        p.leaf_cap = int(leaf_cap)
+        p.precision = int(precision)
+        p.q[0], p.q[1] = float(q[0]), float(q[1])
+        p.m[0], p.m[1] = float(m[0]), float(m[1])
+        if stream is None:
+            try:
+                import torch
+                if torch.cuda.is_available():
+                    stream = torch.cuda.current_stream().cuda_stream
+            except ImportError:
+                stream = None
+        p.cuda_stream = stream
+        self.n = int(n)
+        self._h = C.c_void_p()
+        rc = L.ucp_create(C.byref(self._h), C.byref(p))
+        if rc:
+            raise UcpError(rc, "ucp_create: " + L.ucp_strerror(rc).decode())
+
+    def _check(self, rc, what):
+        if rc:
+            msg = lib().ucp_last_error(self._h).decode()
+            raise UcpError(rc, f"{what}: {lib().ucp_strerror(rc).decode()}: {msg}")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().ucp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- state
+    def set_state(self, pos, vel, species):
+        pp, d1 = _ptr(pos, np.float64)
+        vp, d2 = _ptr(vel, np.float64)
+        sp, d3 = _ptr(species, np.int8)
+        if not (d1 == d2 == d3):
+            raise TypeError("pos, vel and species must all be host or all device arrays")
+        self._check(lib().ucp_set_state(self._h, pp, vp, sp, d1), "ucp_set_state")
+
+    def get_state(self, pos=None, vel=None):
+        if pos is None and vel is None:
+            pos = np.empty((self.n, 3))
+            vel = np.empty((self.n, 3))
+        pp, d1 = _ptr(pos, np.float64)
+        vp, d2 = _ptr(vel, np.float64)
+        self._check(lib().ucp_get_state(self._h, pp, vp, max(d1, d2)), "ucp_get_state")
+        return pos, vel
+
+    # -- the hot path
+    def tree_build(self):
+        self._check(lib().ucp_tree_build(self._h), "ucp_tree_build")
+
+    def tree_force(self, theta, eps, acc=None, phi=None, want=True):
+        """Accelerations (N, 3) and potentials (N,) in caller order; host
+        arrays are allocated when none are given and ``want`` is true."""
+        if acc is None and phi is None and want:
+            acc = np.empty((self.n, 3))
+            phi = np.empty(self.n)
+        ap, d1 = _ptr(acc, np.float64)
+        pp, d2 = _ptr(phi, np.float64)
+        self._check(lib().ucp_tree_force(self._h, float(theta), float(eps), ap, pp, max(d1, d2)),
+                    "ucp_tree_force")
+        return acc, phi
+
+    def step(self, dt_e, ion_substep_ratio, n_electron_steps, theta, eps):
+        self._check(lib().ucp_step(self._h, float(dt_e), int(ion_substep_ratio),
+                                   int(n_electron_steps), float(theta), float(eps)), "ucp_step")
+
+    def energy(self, theta, eps):
+        out = np.zeros(6)
+        self._check(lib().ucp_energy(self._h, float(theta), float(eps), out.ctypes.data),
+                    "ucp_energy")
+        return out
+
+    def stats(self, reset=False):
+        out = np.zeros(8, dtype=np.int64)
+        self._check(lib().ucp_stats(self._h, out.ctypes.data, int(reset)), "ucp_stats")
+        return out
+
+    # -- inspection
+    def get_cube(self):
+        out = np.zeros(4)
+        self._check(lib().ucp_get_cube(self._h, out.ctypes.data), "ucp_get_cube")
+        return out
+
+    def get_sorted(self):
+        keys = np.zeros(self.n, dtype=np.uint64)
+        ids = np.zeros(self.n, dtype=np.uint32)
+        self._check(lib().ucp_get_sorted(self._h, keys.ctypes.data, ids.ctypes.data, 0),
+                    "ucp_get_sorted")
+        return keys, ids
+
+    def get_tree(self):
+        nn = C.c_int64(0)
+        self._check(lib().ucp_get_tree(self._h, C.byref(nn), 0, None, None, None), "ucp_get_tree")
+        k = nn.value
+        topo = np.zeros((k, 4), dtype=np.int32)
+        leaf = np.zeros(k, dtype=np.int8)
+        geom = np.zeros((k, 20))
+        self._check(lib().ucp_get_tree(self._h, C.byref(nn), k, topo.ctypes.data,
+                                       leaf.ctypes.data, geom.ctypes.data), "ucp_get_tree")
+        return {"begin": topo[:, 0], "end": topo[:, 1], "next": topo[:, 2], "depth": topo[:, 3],
+                "is_leaf": leaf.astype(bool), "centre": geom[:, 0:3], "side": geom[:, 3],
+                "S0": geom[:, 4], "M": geom[:, 5], "c": geom[:, 6:9], "D": geom[:, 9:12],
+                "Q": geom[:, 12:18], "delta": geom[:, 18]}
+
+    def get_counts(self):
+        p2p = np.zeros(self.n, dtype=np.int32)
+        m2p = np.zeros(self.n, dtype=np.int32)
+        self._check(lib().ucp_get_counts(self._h, p2p.ctypes.data, m2p.ctypes.data, 0),
+                    "ucp_get_counts")
+        return p2p, m2p
+
+    def profile(self, enable=True):
+        self._check(lib().ucp_profile(self._h, int(bool(enable))), "ucp_profile")
+
+    def profile_read(self):
+        ms = C.c_double(0.0)
+        n = C.c_int64(0)
+        self._check(lib().ucp_profile_read(self._h, C.byref(ms), C.byref(n)), "ucp_profile_read")
+        return ms.value, n.value

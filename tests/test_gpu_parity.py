@@ -1,0 +1,313 @@
+"""GPU path vs the FP64 CPU oracle on the same seeded inputs, through the C ABI.
+
+Bars: integer work (cube, keys, sort order, box table) bit-exact; FP64 force
+relative RMS <= 1e-5 and FP32C <= 1e-4 against the oracle tree (north-star
+tolerances), per-target interaction counts identical up to opening decisions
+that sit within rounding of the criterion; short trajectories pointwise.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_0709_3331_gb300.inputs import gaussian_cloud
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-5
+FP32C_TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def U():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_0709_3331_gb300 import build as b
+    b.build()
+    import paper_0709_3331_gb300 as P
+    return P
+
+
+def _ctx(U, c, leaf_cap, prec):
+    ctx = U.Context(c.n, c.q, c.m, leaf_cap=leaf_cap, precision=prec)
+    ctx.set_state(c.pos, c.vel, c.species)
+    return ctx
+
+
+def rel_rms(a, b):
+    den = (b**2).sum()
+    return math.sqrt(((a - b) ** 2).sum() / den) if den > 0 else float(np.abs(a - b).max())
+
+
+# ----------------------------------------------------------------- a1-a3
+@pytest.mark.parametrize("n,sigma,seed", [(2048, 1.0, 1), (1, 1.0, 3), (2, 1.0, 4),
+                                          (4097 + 1, 2.0, 5), (70000, 4.0, 6)])
+def test_cube_keys_sort_bit_exact(U, orc, n, sigma, seed):
+    c = gaussian_cloud(n + (n % 2), sigma, seed)
+    with _ctx(U, c, 8, U.UCP_FP64) as ctx:
+        ctx.tree_build()
+        cube = ctx.get_cube()
+        keys, ids = ctx.get_sorted()
+    ocube = orc.root_cube(c.pos)
+    assert np.array_equal(cube, ocube)
+    okeys = orc.keys(c.pos, ocube)
+    order = orc.sort_order(okeys)
+    assert np.array_equal(ids.astype(np.int64), order)
+    assert np.array_equal(keys, okeys[order])
+
+
+def test_sort_ties_by_index(U, orc):
+    # many coincident particles: equal keys must come out in index order
+    c = gaussian_cloud(512, 1.0, 7)
+    pos = c.pos.copy()
+    pos[::3] = pos[0]
+    pos[1::7] = pos[5]
+    with U.Context(c.n, c.q, c.m, leaf_cap=4) as ctx:
+        ctx.set_state(pos, c.vel, c.species)
+        ctx.tree_build()
+        keys, ids = ctx.get_sorted()
+    ok = orc.keys(pos)
+    assert np.array_equal(ids.astype(np.int64), orc.sort_order(ok))
+
+
+# ----------------------------------------------------------------- a4-a5
+@pytest.mark.parametrize("leaf_cap", [1, 4, 16])
+@pytest.mark.parametrize("n,sigma,seed", [(2048, 1.0, 1), (3000, 1.5, 9)])
+def test_box_table(U, orc, leaf_cap, n, sigma, seed):
+    c = gaussian_cloud(n, sigma, seed)
+    with _ctx(U, c, leaf_cap, U.UCP_FP64) as ctx:
+        ctx.tree_build()
+        g = ctx.get_tree()
+        _, ids = ctx.get_sorted()
+    T = orc.Tree(c.pos, c.species, c.q, leaf_cap=leaf_cap)
+    o = T.export()
+    assert len(g["begin"]) == T.nnodes
+    for k in ("begin", "end", "next", "depth"):
+        assert np.array_equal(g[k].astype(np.int64), o[k]), k
+    assert np.array_equal(g["is_leaf"], o["is_leaf"])
+    assert np.array_equal(g["centre"], o["centre"])
+    assert np.array_equal(g["side"], o["side"])
+    for b, e in zip(o["begin"][o["is_leaf"]], o["end"][o["is_leaf"]]):
+        assert set(ids[b:e].tolist()) == set(o["slot"][b:e].tolist())
+    scale = np.abs(c.pos).max()
+    s0 = o["S0"][:, None]
+
+    def close(a, b, tol):
+        ratio = (np.abs(a - b) / tol).max()
+        assert ratio <= 1.0, ratio
+
+    close(g["M"], o["M"], 1e-12 * n)
+    close(g["S0"], o["S0"], 1e-13 * o["S0"])
+    close(g["c"], o["c"], 1e-13 * scale)
+    close(g["D"], o["D"], 1e-12 * scale * s0)
+    close(g["Q"], o["Q"], 1e-12 * scale**2 * s0)
+    close(g["delta"], o["delta"], 1e-12 * scale)
+
+
+# ----------------------------------------------------------------- a6 (+a9)
+CASES = [
+    # n, sigma, seed, leaf_cap, theta
+    (2048, 1.0, 1, 8, 0.5),      # the small standard workload
+    (2048, 1.0, 1, 1, 0.5),      # the paper's one-particle leaves
+    (2048, 1.0, 1, 16, 0.3),
+    (2048, 1.0, 1, 16, 0.7),
+    (2048, 1.0, 1, 16, 1.0),
+    (1030, 1.0, 11, 16, 0.0),    # theta = 0 reduces to the direct sum; ragged warp tail
+    (34, 0.5, 12, 4, 0.5),       # fewer targets than a warp
+    (20000, 2.0, 13, 16, 0.5),   # many tiles
+]
+
+
+@pytest.mark.parametrize("n,sigma,seed,leaf_cap,theta", CASES)
+def test_force_fp64(U, orc, n, sigma, seed, leaf_cap, theta):
+    c = gaussian_cloud(n, sigma, seed)
+    eps = 0.01
+    T = orc.Tree(c.pos, c.species, c.q, leaf_cap=leaf_cap)
+    E, phi, npp, nmp = T.force(theta, eps, counts=True, nthreads=4)
+    a_ref = E * (c.q[c.species] / c.m[c.species])[:, None]
+    with _ctx(U, c, leaf_cap, U.UCP_FP64) as ctx:
+        acc, ph = ctx.tree_force(theta, eps)
+        gp, gm = ctx.get_counts()
+        st = ctx.stats()
+    assert rel_rms(acc, a_ref) <= FP64_TOL
+    assert rel_rms(ph, phi) <= FP64_TOL
+    # opening decisions agree except where the criterion is within rounding
+    mism = np.count_nonzero((gp != npp) | (gm != nmp))
+    assert mism <= max(1, n // 10000), mism
+    assert st[0] == gp.sum() and st[1] == gm.sum()
+
+
+@pytest.mark.parametrize("n,sigma,seed,leaf_cap,theta", CASES)
+def test_force_fp32c(U, orc, n, sigma, seed, leaf_cap, theta):
+    c = gaussian_cloud(n, sigma, seed)
+    eps = 0.01
+    T = orc.Tree(c.pos, c.species, c.q, leaf_cap=leaf_cap)
+    E, phi = T.force(theta, eps, nthreads=4)
+    a_ref = E * (c.q[c.species] / c.m[c.species])[:, None]
+    with _ctx(U, c, leaf_cap, U.UCP_FP32C) as ctx:
+        acc, ph = ctx.tree_force(theta, eps)
+    assert rel_rms(acc, a_ref) <= FP32C_TOL
+    assert rel_rms(ph, phi) <= FP32C_TOL
+
+
+def test_force_edge_cases(U, orc):
+    eps = 0.05
+    # one particle: no force, no potential
+    c1 = gaussian_cloud(2, 1.0, 1)
+    with U.Context(1, c1.q, c1.m, leaf_cap=1) as ctx:
+        ctx.set_state(c1.pos[:1].copy(), c1.vel[:1].copy(), c1.species[:1].copy())
+        acc, ph = ctx.tree_force(0.5, eps)
+    assert np.all(acc == 0) and np.all(ph == 0)
+    # coincident particles end in one depth-21 box
+    pos = np.repeat(np.array([[0.5, -0.25, 2.0]]), 6, axis=0)
+    pos[5] += 1.0
+    sp = np.array([0, 1, 0, 1, 0, 1], dtype=np.int8)
+    vel = np.zeros((6, 3))
+    for prec in (U.UCP_FP64, U.UCP_FP32C):
+        with U.Context(6, (1.0, -1.0), (1000.0, 1.0), leaf_cap=1, precision=prec) as ctx:
+            ctx.set_state(pos, vel, sp)
+            acc, ph = ctx.tree_force(0.5, eps)
+            g = ctx.get_tree()
+        E, phi = orc.direct(pos, sp, [1.0, -1.0], eps)
+        a_ref = E * (np.array([1.0, -1.0])[sp] / np.array([1000.0, 1.0])[sp])[:, None]
+        assert g["depth"].max() == 21
+        np.testing.assert_allclose(acc, a_ref, rtol=1e-5, atol=1e-6 * np.abs(a_ref).max())
+        np.testing.assert_allclose(ph, phi, rtol=1e-5)
+    # leaf_cap >= N: the root is a leaf and the walk is the direct sum
+    c = gaussian_cloud(300, 1.0, 2)
+    E, phi = orc.direct(c.pos, c.species, c.q, eps)
+    a_ref = E * (c.q[c.species] / c.m[c.species])[:, None]
+    with _ctx(U, c, 512, U.UCP_FP64) as ctx:
+        acc, _ = ctx.tree_force(0.5, eps)
+        assert len(ctx.get_tree()["begin"]) == 1
+    assert rel_rms(acc, a_ref) < 1e-13
+
+
+def test_single_species_and_zero_charge(U, orc):
+    c = gaussian_cloud(2048, 1.0, 21)
+    sp = np.zeros(c.n, dtype=np.int8)
+    q = np.array([1.0, 0.0])
+    T = orc.Tree(c.pos, sp, q, leaf_cap=8)
+    E, phi = T.force(0.5, 0.01)
+    with U.Context(c.n, q, c.m, leaf_cap=8) as ctx:
+        ctx.set_state(c.pos, c.vel, sp)
+        acc, ph = ctx.tree_force(0.5, 0.01)
+    assert rel_rms(acc, E / c.m[0]) <= FP64_TOL
+    sp2 = c.species.copy()
+    T2 = orc.Tree(c.pos, sp2, q, leaf_cap=8)
+    E2, _ = T2.force(0.5, 0.01)
+    with U.Context(c.n, q, c.m, leaf_cap=8, precision=U.UCP_FP32C) as ctx:
+        ctx.set_state(c.pos, c.vel, sp2)
+        acc2, _ = ctx.tree_force(0.5, 0.01)
+    a_ref2 = E2 * (q[sp2] / c.m[sp2])[:, None]
+    assert rel_rms(acc2, a_ref2) <= FP32C_TOL
+
+
+# ----------------------------------------------------------------- a7-a8
+@pytest.mark.parametrize("prec,tol", [(0, 1e-9), (1, 1e-6)])
+def test_step_trajectory(U, orc, prec, tol):
+    c = gaussian_cloud(2048, 1.0, 1)
+    theta, eps, leaf = 0.5, 0.01, 8
+    p_ref, v_ref, _ = orc.run(c.pos, c.vel, c.species, c.q, c.m, 1e-3, 10, 1, theta, eps,
+                              leaf_cap=leaf, nthreads=4)
+    with _ctx(U, c, leaf, prec) as ctx:
+        ctx.step(1e-3, 10, 10, theta, eps)
+        pos, vel = ctx.get_state()
+        out = ctx.energy(theta, eps)
+    scale = np.abs(c.pos).max()
+    assert np.abs(pos - p_ref).max() <= tol * scale
+    vs = np.abs(v_ref).max()
+    assert np.abs(vel - v_ref).max() <= 1e3 * tol * vs
+    e_ref = orc.energy(p_ref, v_ref, c.species, c.q, c.m, theta, eps, leaf_cap=leaf)
+    np.testing.assert_allclose(out[:2], e_ref[:2], rtol=1e3 * tol)
+    assert abs(out[2] - e_ref[2]) <= 1e2 * max(tol, 1e-6) * (abs(e_ref[0]) + abs(e_ref[1]))
+    assert out[5] == 10
+
+
+def test_step_k1_and_blocks(U, orc):
+    c = gaussian_cloud(512, 1.0, 17)
+    theta, eps, leaf = 0.4, 0.02, 4
+    p_ref, v_ref, _ = orc.run(c.pos, c.vel, c.species, c.q, c.m, 2e-3, 1, 6, theta, eps,
+                              leaf_cap=leaf)
+    p_ref2, v_ref2, _ = orc.run(c.pos, c.vel, c.species, c.q, c.m, 1e-3, 3, 2, theta, eps,
+                                leaf_cap=leaf)
+    with _ctx(U, c, leaf, U.UCP_FP64) as ctx:
+        ctx.step(2e-3, 1, 6, theta, eps)
+        pos, vel = ctx.get_state()
+    assert np.abs(pos - p_ref).max() < 1e-10
+    with _ctx(U, c, leaf, U.UCP_FP64) as ctx:
+        ctx.step(1e-3, 3, 3, theta, eps)   # two calls of one block each == one call of two
+        ctx.step(1e-3, 3, 3, theta, eps)
+        pos2, vel2 = ctx.get_state()
+    assert np.abs(pos2 - p_ref2).max() < 1e-10
+    assert np.abs(vel2 - v_ref2).max() < 1e-7
+
+
+def test_energy_matches_oracle(U, orc):
+    c = gaussian_cloud(2048, 1.0, 1)
+    e_ref = orc.energy(c.pos, c.vel, c.species, c.q, c.m, 0.5, 0.01, leaf_cap=8)
+    with _ctx(U, c, 8, U.UCP_FP64) as ctx:
+        out = ctx.energy(0.5, 0.01)
+    np.testing.assert_allclose(out[:4], e_ref[:4], rtol=1e-11)
+    assert out[4] < 1e-10
+
+
+def test_resume_bit_exact(U):
+    c = gaussian_cloud(4096, 1.5, 23)
+    with _ctx(U, c, 16, U.UCP_FP32C) as ctx:
+        ctx.step(1e-3, 5, 10, 0.5, 0.01)
+        p1, v1 = ctx.get_state()
+    with _ctx(U, c, 16, U.UCP_FP32C) as ctx:
+        ctx.step(1e-3, 5, 5, 0.5, 0.01)
+        pm, vm = ctx.get_state()
+    with U.Context(c.n, c.q, c.m, leaf_cap=16, precision=U.UCP_FP32C) as ctx:
+        ctx.set_state(pm, vm, c.species)   # checkpoint restart recomputes a(x) first
+        ctx.step(1e-3, 5, 5, 0.5, 0.01)
+        p2, v2 = ctx.get_state()
+    assert np.array_equal(p1, p2) and np.array_equal(v1, v2)
+
+
+# ----------------------------------------------------------------- errors
+def test_error_codes(U):
+    c = gaussian_cloud(64, 1.0, 1)
+    ctx = U.Context(c.n, c.q, c.m, leaf_cap=4)
+    with pytest.raises(U.UcpError) as e:
+        ctx.tree_build()
+    assert e.value.code == -6
+    bad = c.pos.copy()
+    bad[3, 1] = np.nan
+    with pytest.raises(U.UcpError) as e:
+        ctx.set_state(bad, c.vel, c.species)
+    assert e.value.code == -4
+    sp = c.species.copy()
+    sp[0] = 3
+    with pytest.raises(U.UcpError) as e:
+        ctx.set_state(c.pos, c.vel, sp)
+    assert e.value.code == -1
+    ctx.set_state(c.pos, c.vel, c.species)
+    for args in ((0.0, 1, 10, 0.5, 0.01), (1e-3, 0, 10, 0.5, 0.01), (1e-3, 3, 10, 0.5, 0.01),
+                 (1e-3, 1, 10, 1.5, 0.01), (1e-3, 1, 10, 0.5, -1.0)):
+        with pytest.raises(U.UcpError) as e:
+            ctx.step(*args)
+        assert e.value.code == -1
+    ctx.step(1e-3, 1, 2, 0.5, 0.01)   # still usable after rejected calls
+    ctx.close()
+
+
+def test_device_pointers(U, orc):
+    import torch
+    c = gaussian_cloud(4096, 1.0, 31)
+    dev = torch.device("cuda")
+    pos = torch.from_numpy(c.pos).to(dev)
+    vel = torch.from_numpy(c.vel).to(dev)
+    sp = torch.from_numpy(c.species).to(dev)
+    acc = torch.empty((c.n, 3), dtype=torch.float64, device=dev)
+    phi = torch.empty(c.n, dtype=torch.float64, device=dev)
+    with U.Context(c.n, c.q, c.m, leaf_cap=16) as ctx:
+        ctx.set_state(pos, vel, sp)
+        ctx.tree_force(0.5, 0.01, acc, phi)
+        torch.cuda.synchronize()
+        a_host, p_host = ctx.tree_force(0.5, 0.01)
+    assert np.array_equal(acc.cpu().numpy(), a_host)
+    assert np.array_equal(phi.cpu().numpy(), p_host)
