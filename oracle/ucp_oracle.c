@@ -24,8 +24,9 @@
  *       softening replaces the Kelbg form of Eq. 3 for the e-i pair).
  *   R2  enclosing cube: centre = (min+max)/2 per axis, side L = (largest
  *       extent) * (1 + 2^-20); L = 1 when all particles coincide.
- *   R3  integer cell coordinates k = floor(((x - lo) / L) * 2^21) clamped to
- *       [0, 2^21 - 1] with lo = centre - L/2; a box at depth d holds the
+ *   R3  integer cell coordinates k = floor((x - lo) * (2^21 / L)) clamped to
+ *       [0, 2^21 - 1] with lo = centre - L/2 and the scale 2^21 / L rounded
+ *       once (even subdivision of the cube); a box at depth d holds the
  *       particles whose k agree in their top d bits; depth is capped at 21,
  *       so coincident particles end in one (fat) leaf.
  *   R4  pseudo-particle position (Sec. 3, "interpolated ... depending on the
@@ -140,10 +141,11 @@ void orc_root_cube(int64_t n, const double* pos, double out[4])
 void orc_int_coords(int64_t n, const double* pos, const double cube[4], uint32_t* k)
 {
     double L = cube[3];
+    double scale = (double)ORC_KMAX / L;
     for (int64_t i = 0; i < n; ++i)
         for (int a = 0; a < 3; ++a) {
             double lo = cube[a] - L * 0.5;
-            double u = floor(((pos[3 * i + a] - lo) / L) * (double)ORC_KMAX);
+            double u = floor((pos[3 * i + a] - lo) * scale);
             uint32_t v;
             if (!(u > 0.0)) v = 0;                       /* also catches u = -0 */
             else if (u >= (double)(ORC_KMAX - 1)) v = ORC_KMAX - 1;

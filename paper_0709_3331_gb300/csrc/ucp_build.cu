@@ -144,20 +144,37 @@ __global__ void k_bbox_partial(const double* __restrict__ x, const double* __res
 // side 1 when all particles coincide.
 __global__ void k_bbox_final(const double* __restrict__ part, int nblk, Cube* cube)
 {
-    if (threadIdx.x != 0) return;
+    __shared__ double s[256][6];
     double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
-    for (int b = 0; b < nblk; ++b)
+    for (int b = threadIdx.x; b < nblk; b += blockDim.x)
         for (int a = 0; a < 3; ++a) {
             lo[a] = fmin(lo[a], part[6 * b + a]);
             hi[a] = fmax(hi[a], part[6 * b + 3 + a]);
         }
+    for (int a = 0; a < 3; ++a) {
+        s[threadIdx.x][a] = lo[a];
+        s[threadIdx.x][3 + a] = hi[a];
+    }
+    __syncthreads();
+    for (int st = 128; st > 0; st >>= 1) {
+        if ((int)threadIdx.x < st)
+            for (int a = 0; a < 3; ++a) {
+                s[threadIdx.x][a] = fmin(s[threadIdx.x][a], s[threadIdx.x + st][a]);
+                s[threadIdx.x][3 + a] = fmax(s[threadIdx.x][3 + a], s[threadIdx.x + st][3 + a]);
+            }
+        __syncthreads();
+    }
+    if (threadIdx.x != 0) return;
     double ext = 0.0;
     for (int a = 0; a < 3; ++a) {
-        cube->c[a] = __dmul_rn(__dadd_rn(lo[a], hi[a]), 0.5);
-        double e = __dsub_rn(hi[a], lo[a]);
+        cube->c[a] = __dmul_rn(__dadd_rn(s[0][a], s[0][3 + a]), 0.5);
+        double e = __dsub_rn(s[0][3 + a], s[0][a]);
         if (e > ext) ext = e;
     }
-    cube->L = ext > 0.0 ? __dmul_rn(ext, 1.0 + 0x1p-20) : 1.0;
+    double L = ext > 0.0 ? __dmul_rn(ext, 1.0 + 0x1p-20) : 1.0;
+    cube->L = L;
+    for (int a = 0; a < 3; ++a) cube->lo[a] = __dsub_rn(cube->c[a], __dmul_rn(L, 0.5));
+    cube->kscale = __ddiv_rn(2097152.0, L);
 }
 
 // ---------------------------------------------------------------- keys
@@ -172,10 +189,10 @@ __device__ __forceinline__ unsigned long long spread3(unsigned int v)
     return x;
 }
 
-__device__ __forceinline__ unsigned int cell_coord(double x, double c, double L)
+// cell coordinate k = floor((x - lo) * (2^21 / L)), clamped to [0, 2^21 - 1]
+__device__ __forceinline__ unsigned int cell_coord(double x, double lo, double kscale)
 {
-    double lo = __dsub_rn(c, __dmul_rn(L, 0.5));
-    double u = floor(__dmul_rn(__ddiv_rn(__dsub_rn(x, lo), L), 2097152.0));
+    double u = floor(__dmul_rn(__dsub_rn(x, lo), kscale));
     if (!(u > 0.0)) return 0u;
     if (u >= 2097151.0) return 2097151u;
     return (unsigned int)u;
@@ -187,10 +204,10 @@ __global__ void k_keys(const double* __restrict__ x, const double* __restrict__ 
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    double L = cube->L;
-    unsigned int kx = cell_coord(x[i], cube->c[0], L);
-    unsigned int ky = cell_coord(y[i], cube->c[1], L);
-    unsigned int kz = cell_coord(z[i], cube->c[2], L);
+    double ks = cube->kscale;
+    unsigned int kx = cell_coord(x[i], cube->lo[0], ks);
+    unsigned int ky = cell_coord(y[i], cube->lo[1], ks);
+    unsigned int kz = cell_coord(z[i], cube->lo[2], ks);
     key[i] = spread3(kx) | (spread3(ky) << 1) | (spread3(kz) << 2);
     val[i] = (unsigned int)i;
 }
@@ -588,7 +605,7 @@ void launch_bbox(const double* x, const double* y, const double* z, int n, doubl
 {
     count_launch(2);
     k_bbox_partial<<<nblk, 256, 0, s>>>(x, y, z, n, partials);
-    k_bbox_final<<<1, 32, 0, s>>>(partials, nblk, cube);
+    k_bbox_final<<<1, 256, 0, s>>>(partials, nblk, cube);
 }
 
 void launch_keys(const double* x, const double* y, const double* z, int n, const Cube* cube,

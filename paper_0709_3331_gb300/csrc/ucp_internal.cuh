@@ -41,11 +41,14 @@ struct Tree {
     double* mom;             // kMom doubles per box
     float4* f32;             // kF32 float4 per box
     int* arrive;             // bottom-up arrival counters (particles)
+    int* child8;             // 8 child slots per box (octant order), -1 = empty
 };
 
-struct Cube {                // enclosing cube: centre and side
+struct Cube {                // enclosing cube: centre, side, lower corner, 2^21 / side
     double c[3];
     double L;
+    double lo[3];
+    double kscale;
 };
 
 // ---- build (ucp_build.cu) ----
