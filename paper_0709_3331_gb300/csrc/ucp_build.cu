@@ -423,10 +423,12 @@ __global__ void k_topo_emit(const unsigned long long* __restrict__ K, int n, int
         bool leaf = (e - i <= leaf_cap) || d == kMaxDepth;
         int nx = e < n ? off[e] : nn;
         if (node >= t.cap) break;  // cannot happen: the capacity bounds the box count
+        unsigned long long pre = prefix_at(K[i], d);
         t.info[node] = make_int4(i, e, nx, parent);
         t.depth_leaf[node] = d | (leaf ? 256 : 0);
-        t.cell[node] = prefix_at(K[i], d);
+        t.cell[node] = pre;
         t.arrive[node] = 0;
+        if (parent >= 0) t.child8[(size_t)parent * 8 + (int)(pre & 7ull)] = node;
         parent = node;
         ++node;
         dmax = d;
@@ -460,125 +462,162 @@ __device__ __forceinline__ void box_centre(const Cube& cb, unsigned long long ce
     }
 }
 
-__device__ void finish_box(double* __restrict__ m, const double ctr[3])
+// Moments of one box from sums about its geometric centre z:
+//   a = {S0, M, sum|q|y (3), sum q y (3), sum q y y^T (6)},  y = x - z.
+// The expansion centre is the |q|-weighted centroid c = z + e, e = sum|q|y / S0
+// (z when S0 = 0); shifting to c: D = sum q y - M e,
+// Q = sum q y y^T - (sum q y) e^T - e (sum q y)^T + M e e^T.  delta = |e|.
+__device__ __forceinline__ void finish_box(const double* a, const double z[3],
+                                           double* __restrict__ m)
 {
-    double ex = __dsub_rn(m[MC + 0], ctr[0]);
-    double ey = __dsub_rn(m[MC + 1], ctr[1]);
-    double ez = __dsub_rn(m[MC + 2], ctr[2]);
+    double S0 = a[0], M = a[1];
+    double e[3];
+    for (int k = 0; k < 3; ++k) e[k] = S0 > 0.0 ? a[2 + k] / S0 : 0.0;
+    double d[3];
+    for (int k = 0; k < 3; ++k) d[k] = a[5 + k];
+    m[MC + 0] = z[0] + e[0];
+    m[MC + 1] = z[1] + e[1];
+    m[MC + 2] = z[2] + e[2];
+    m[MM] = M;
+    for (int k = 0; k < 3; ++k) m[MD + k] = d[k] - M * e[k];
+    const int ia[6] = {0, 0, 0, 1, 1, 2}, ib[6] = {0, 1, 2, 1, 2, 2};
+    for (int k = 0; k < 6; ++k)
+        m[MQ + k] = a[8 + k] - d[ia[k]] * e[ib[k]] - e[ia[k]] * d[ib[k]] + M * e[ia[k]] * e[ib[k]];
+    m[MS0] = S0;
+    // delta = |c - z| rounded like the definition: c is stored first, then differenced
+    double ex = __dsub_rn(m[MC + 0], z[0]);
+    double ey = __dsub_rn(m[MC + 1], z[1]);
+    double ez = __dsub_rn(m[MC + 2], z[2]);
     m[MDELTA] = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)),
                                      __dmul_rn(ez, ez)));
 }
 
-// Moments of each leaf from its particles; a box is finished by the last of
-// its children to complete (arrival counted in particles), which combines the
-// children's moments about the box's own centroid (parallel-axis shift).
-__global__ void k_moments(const double* __restrict__ x, const double* __restrict__ y,
-                          const double* __restrict__ z, const int8_t* __restrict__ sp,
-                          const double* __restrict__ qsp, const Cube* __restrict__ cube, Tree t,
-                          float4* __restrict__ src32, int want_f32)
+__device__ __forceinline__ double warp_sum(double v)
 {
-    int nn = *t.nnodes;
-    Cube cb = *cube;
-    double q0 = qsp[0], q1 = qsp[1];
-    for (int node = blockIdx.x * blockDim.x + threadIdx.x; node < nn;
-         node += gridDim.x * blockDim.x) {
-        int dl = t.depth_leaf[node];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__global__ void k_clear_children(Tree t)
+{
+    int total = *t.nnodes * 8;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x)
+        t.child8[i] = -1;
+}
+
+// One warp per box.  A leaf sums its particles (lanes stride the key-ordered
+// range, coalesced); a twig is finished by the warp whose child completes the
+// twig's particle count (arrival counter), which gathers the eight child slots
+// in lanes 0-7 and shifts each child's moments to the twig's centre.  Results
+// do not depend on which warp finishes a twig.
+__global__ void __launch_bounds__(256)
+k_moments(const double* __restrict__ x, const double* __restrict__ y,
+          const double* __restrict__ z, const int8_t* __restrict__ sp,
+          const double* __restrict__ qsp, const Cube* __restrict__ cube, Tree t,
+          float4* __restrict__ src32, int want_f32)
+{
+    const int lane = threadIdx.x & 31;
+    const int nw = gridDim.x * (blockDim.x >> 5);
+    const int nn = *t.nnodes;
+    const Cube cb = *cube;
+    const double q0 = qsp[0], q1 = qsp[1];
+    for (int node = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); node < nn; node += nw) {
+        const int dl = t.depth_leaf[node];
         if (!(dl & 256)) continue;
-        int4 inf = t.info[node];
-        double ctr[3], side;
-        box_centre(cb, t.cell[node], dl & 255, ctr, &side);
-        double S0 = 0.0, M = 0.0, w[3] = {0.0, 0.0, 0.0};
-        for (int j = inf.x; j < inf.y; ++j) {
+        const int4 inf = t.info[node];
+        double zc[3], side;
+        box_centre(cb, t.cell[node], dl & 255, zc, &side);
+        double a[14];
+#pragma unroll
+        for (int k = 0; k < 14; ++k) a[k] = 0.0;
+        for (int j = inf.x + lane; j < inf.y; j += 32) {
             double qj = sp[j] ? q1 : q0;
             double aq = fabs(qj);
-            S0 += aq;
-            M += qj;
-            w[0] += aq * x[j];
-            w[1] += aq * y[j];
-            w[2] += aq * z[j];
-        }
-        double c[3];
-        for (int a = 0; a < 3; ++a) c[a] = S0 > 0.0 ? w[a] / S0 : ctr[a];
-        double D[3] = {0, 0, 0}, Q[6] = {0, 0, 0, 0, 0, 0};
-        for (int j = inf.x; j < inf.y; ++j) {
-            double qj = sp[j] ? q1 : q0;
-            double yx = x[j] - c[0], yy = y[j] - c[1], yz = z[j] - c[2];
-            D[0] += qj * yx;
-            D[1] += qj * yy;
-            D[2] += qj * yz;
-            Q[0] += qj * yx * yx;
-            Q[1] += qj * yx * yy;
-            Q[2] += qj * yx * yz;
-            Q[3] += qj * yy * yy;
-            Q[4] += qj * yy * yz;
-            Q[5] += qj * yz * yz;
-            if (want_f32) {
-                float ox = (float)yx, oy = (float)yy, oz = (float)yz;
-                src32[j] = make_float4(ox, oy, oz, (float)qj);
+            double yv[3] = {x[j] - zc[0], y[j] - zc[1], z[j] - zc[2]};
+            a[0] += aq;
+            a[1] += qj;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                a[2 + k] += aq * yv[k];
+                a[5 + k] += qj * yv[k];
             }
+            a[8] += qj * yv[0] * yv[0];
+            a[9] += qj * yv[0] * yv[1];
+            a[10] += qj * yv[0] * yv[2];
+            a[11] += qj * yv[1] * yv[1];
+            a[12] += qj * yv[1] * yv[2];
+            a[13] += qj * yv[2] * yv[2];
         }
-        double* m = t.mom + (size_t)node * kMom;
-        m[MC + 0] = c[0];
-        m[MC + 1] = c[1];
-        m[MC + 2] = c[2];
-        m[MM] = M;
-        for (int a = 0; a < 3; ++a) m[MD + a] = D[a];
-        for (int a = 0; a < 6; ++a) m[MQ + a] = Q[a];
-        m[MS0] = S0;
-        finish_box(m, ctr);
+#pragma unroll
+        for (int k = 0; k < 14; ++k) a[k] = warp_sum(a[k]);
+        double rec[kMom];
+        finish_box(a, zc, rec);
+        if (lane == 0) {
+            double* m = t.mom + (size_t)node * kMom;
+#pragma unroll
+            for (int k = 0; k < kMom; ++k) m[k] = rec[k];
+        }
+        if (want_f32)
+            for (int j = inf.x + lane; j < inf.y; j += 32) {
+                double qj = sp[j] ? q1 : q0;
+                src32[j] = make_float4((float)(x[j] - rec[MC]), (float)(y[j] - rec[MC + 1]),
+                                       (float)(z[j] - rec[MC + 2]), (float)qj);
+            }
 
-        // climb: the child that completes a box's particle count finishes it
         int cur = node, cnt = inf.y - inf.x;
         while (true) {
-            int p = t.info[cur].w;
+            const int p = t.info[cur].w;
             if (p < 0) break;
-            int4 pin = t.info[p];
-            int pc = pin.y - pin.x;
-            __threadfence();
-            int old = atomicAdd(&t.arrive[p], cnt);
-            if (old + cnt != pc) break;
-            __threadfence();
-            double S = 0.0, MM_ = 0.0, ww[3] = {0, 0, 0};
-            for (int ch = p + 1; ch < pin.z; ch = t.info[ch].z) {
-                const double* cm = t.mom + (size_t)ch * kMom;
-                double s0 = __ldcg(cm + MS0);
-                S += s0;
-                MM_ += __ldcg(cm + MM);
-                for (int a = 0; a < 3; ++a) ww[a] += s0 * __ldcg(cm + MC + a);
+            const int4 pin = t.info[p];
+            const int pc = pin.y - pin.x;
+            int last = 0;
+            if (lane == 0) {
+                __threadfence();
+                int old = atomicAdd(&t.arrive[p], cnt);
+                last = old + cnt == pc;
             }
-            int pd = t.depth_leaf[p] & 255;
-            double pctr[3], ps;
-            box_centre(cb, t.cell[p], pd, pctr, &ps);
-            double pcen[3];
-            for (int a = 0; a < 3; ++a) pcen[a] = S > 0.0 ? ww[a] / S : pctr[a];
-            double PD[3] = {0, 0, 0}, PQ[6] = {0, 0, 0, 0, 0, 0};
-            for (int ch = p + 1; ch < pin.z; ch = t.info[ch].z) {
-                const double* cm = t.mom + (size_t)ch * kMom;
-                double mk = __ldcg(cm + MM);
-                double e[3], dk[3], qk[6];
-                for (int a = 0; a < 3; ++a) {
-                    e[a] = __ldcg(cm + MC + a) - pcen[a];
-                    dk[a] = __ldcg(cm + MD + a);
+            if (!__shfl_sync(0xffffffffu, last, 0)) break;
+            __threadfence();
+            const int pd = t.depth_leaf[p] & 255;
+            double zp[3], ps;
+            box_centre(cb, t.cell[p], pd, zp, &ps);
+#pragma unroll
+            for (int k = 0; k < 14; ++k) a[k] = 0.0;
+            if (lane < 8) {
+                const int ch = t.child8[(size_t)p * 8 + lane];
+                if (ch >= 0) {
+                    const double* cm = t.mom + (size_t)ch * kMom;
+                    double S0k = __ldcg(cm + MS0), Mk = __ldcg(cm + MM);
+                    double e[3], dk[3], qk[6];
+                    for (int k = 0; k < 3; ++k) {
+                        e[k] = __ldcg(cm + MC + k) - zp[k];
+                        dk[k] = __ldcg(cm + MD + k);
+                    }
+                    for (int k = 0; k < 6; ++k) qk[k] = __ldcg(cm + MQ + k);
+                    a[0] = S0k;
+                    a[1] = Mk;
+                    for (int k = 0; k < 3; ++k) {
+                        a[2 + k] = S0k * e[k];
+                        a[5 + k] = dk[k] + Mk * e[k];
+                    }
+                    // Q_k + D_k e^T + e D_k^T + M_k e e^T
+                    a[8] = qk[0] + 2.0 * dk[0] * e[0] + Mk * e[0] * e[0];
+                    a[9] = qk[1] + dk[0] * e[1] + e[0] * dk[1] + Mk * e[0] * e[1];
+                    a[10] = qk[2] + dk[0] * e[2] + e[0] * dk[2] + Mk * e[0] * e[2];
+                    a[11] = qk[3] + 2.0 * dk[1] * e[1] + Mk * e[1] * e[1];
+                    a[12] = qk[4] + dk[1] * e[2] + e[1] * dk[2] + Mk * e[1] * e[2];
+                    a[13] = qk[5] + 2.0 * dk[2] * e[2] + Mk * e[2] * e[2];
                 }
-                for (int a = 0; a < 6; ++a) qk[a] = __ldcg(cm + MQ + a);
-                for (int a = 0; a < 3; ++a) PD[a] += dk[a] + mk * e[a];
-                // Q += Q_k + D_k e^T + e D_k^T + M_k e e^T
-                PQ[0] += qk[0] + 2.0 * dk[0] * e[0] + mk * e[0] * e[0];
-                PQ[1] += qk[1] + dk[0] * e[1] + e[0] * dk[1] + mk * e[0] * e[1];
-                PQ[2] += qk[2] + dk[0] * e[2] + e[0] * dk[2] + mk * e[0] * e[2];
-                PQ[3] += qk[3] + 2.0 * dk[1] * e[1] + mk * e[1] * e[1];
-                PQ[4] += qk[4] + dk[1] * e[2] + e[1] * dk[2] + mk * e[1] * e[2];
-                PQ[5] += qk[5] + 2.0 * dk[2] * e[2] + mk * e[2] * e[2];
             }
-            double* pm = t.mom + (size_t)p * kMom;
-            for (int a = 0; a < 3; ++a) {
-                pm[MC + a] = pcen[a];
-                pm[MD + a] = PD[a];
+#pragma unroll
+            for (int k = 0; k < 14; ++k) a[k] = warp_sum(a[k]);
+            finish_box(a, zp, rec);
+            if (lane == 0) {
+                double* m = t.mom + (size_t)p * kMom;
+#pragma unroll
+                for (int k = 0; k < kMom; ++k) m[k] = rec[k];
             }
-            for (int a = 0; a < 6; ++a) pm[MQ + a] = PQ[a];
-            pm[MM] = MM_;
-            pm[MS0] = S;
-            finish_box(pm, pctr);
             cur = p;
             cnt = pc;
         }
@@ -649,10 +688,11 @@ void launch_tiefix(const unsigned long long* key, unsigned int* perm, const unsi
 void launch_topology(const unsigned long long* key, int n, int leaf_cap, int* pos_cnt,
                      int* pos_off, int* scan_part, Tree t, cudaStream_t s)
 {
-    count_launch(2);
+    count_launch(3);
     cudaMemsetAsync(t.maxdepth, 0, sizeof(int), s);
     k_topo_count<<<(n + 255) / 256, 256, 0, s>>>(key, n, leaf_cap, pos_cnt);
     launch_scan(pos_cnt, pos_off, n, scan_part, t.nnodes, s);
+    k_clear_children<<<2 * 152, 256, 0, s>>>(t);
     k_topo_emit<<<(n + 255) / 256, 256, 0, s>>>(key, n, leaf_cap, pos_cnt, pos_off, t);
 }
 
@@ -661,10 +701,7 @@ void launch_moments(const double* x, const double* y, const double* z, const int
                     int want_f32, cudaStream_t s)
 {
     count_launch(1);
-    int blocks = (n + 255) / 256;
-    if (blocks > 4 * 152) blocks = 4 * 152;
-    if (blocks < 1) blocks = 1;
-    k_moments<<<blocks, 256, 0, s>>>(x, y, z, sp, qsp, cube, t, src32, want_f32);
+    k_moments<<<8 * 152, 256, 0, s>>>(x, y, z, sp, qsp, cube, t, src32, want_f32);
 }
 
 }  // namespace ucp

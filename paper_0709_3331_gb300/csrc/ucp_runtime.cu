@@ -323,7 +323,7 @@ int ucp_create(ucp_ctx** out, const ucp_params* p)
     if ((rc = dalloc(c, &c->t.nnodes, 1)) || (rc = dalloc(c, &c->t.maxdepth, 1)) ||
         (rc = dalloc(c, &c->t.info, cz)) || (rc = dalloc(c, &c->t.depth_leaf, cz)) ||
         (rc = dalloc(c, &c->t.cell, cz)) || (rc = dalloc(c, &c->t.mom, cz * kMom)) ||
-        (rc = dalloc(c, &c->t.arrive, cz)))
+        (rc = dalloc(c, &c->t.arrive, cz)) || (rc = dalloc(c, &c->t.child8, cz * 8)))
         return bail(rc);
     if (c->precision == UCP_FP32C) {
         if ((rc = dalloc(c, &c->t.f32, cz * kF32)) || (rc = dalloc(c, &c->src32, n)))

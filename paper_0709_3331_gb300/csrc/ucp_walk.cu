@@ -316,7 +316,19 @@ k_walk_fp32c(WalkArgs a)
             float ry = (yh - A.y) + (yl - B.y);
             float rz = (zh - A.z) + (zl - B.z);
             float d2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
-            const bool acc = active && (A.w < d2);
+            bool acc = active && (A.w < d2);
+            // Within FP32 rounding of the threshold the decision is taken again in
+            // FP64 exactly as the FP64 walk takes it, so both precisions open the
+            // same boxes (rare: |d2 - rcrit2| <= 4e-6 d2).
+            if (active && fabsf(d2 - A.w) <= 4e-6f * d2) {
+                const double* m = a.t.mom + (size_t)node * kMom;
+                double dx = __dsub_rn(a.x[t], m[0]);
+                double dy = __dsub_rn(a.y[t], m[1]);
+                double dz = __dsub_rn(a.z[t], m[2]);
+                double dd = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)),
+                                      __dmul_rn(dz, dz));
+                acc = m[MR2] < dd;
+            }
             const bool opn = active && !acc;
             const unsigned int am = __ballot_sync(0xffffffffu, acc);
             const unsigned int om = __ballot_sync(0xffffffffu, opn);
