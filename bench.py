@@ -39,9 +39,10 @@ WORKLOAD = dict(name="precision_n524288", n=524288, sigma=8.0, seed=3, theta=0.5
 METRIC = "tree-force interactions/s at N=524288 (FP32 compensated walk, FP64 state)"
 UNIT = "interactions/s"
 # Flops charged per interaction by the roofline (counted from the FP32C kernel's
-# inner loops, FMA = 2, rsqrt = 1): direct pair 20, quadrupole multipole 86.
+# arithmetic, FMA = 2, rsqrt = 1): direct pair 20, multipole through quadrupole
+# order 64 (R and |R|^2 come from the opening criterion and are not charged).
 FLOP_P2P = 20
-FLOP_M2P = 86
+FLOP_M2P = 64
 FP32_LANES_PER_SM = 128
 
 
@@ -128,20 +129,26 @@ def oracle_sample(cloud, n_targets, nthreads, seed=0):
     return dt, int(npp.sum() + nmp.sum())
 
 
-def cpu_baseline(cloud, budget_s=15.0):
+def cpu_baseline(cloud, budget_s=12.0):
+    """The oracle as it stands on the host cores: tree build + walk of every
+    particle, repeated until about budget_s seconds of CPU work."""
     from oracle import oracle as O
     O.build()
     cores = os.cpu_count() or 1
     nthreads = cores if O.has_openmp() else 1
-    dt, inter = oracle_sample(cloud, 2048, nthreads)
-    # scale the target sample so the measured leg takes about budget_s
-    per_target = dt / 2048.0
-    nt = int(min(cloud.n, max(2048, budget_s / max(per_target, 1e-9))))
-    dt, inter = oracle_sample(cloud, nt, nthreads, seed=1)
-    return {"value": inter / dt, "unit": UNIT, "cores": nthreads, "kind": "oracle",
-            "sample": f"FP64 serial-tree oracle: tree build over all {cloud.n} particles + "
-                      f"walk of {nt} seeded targets (theta {WORKLOAD['theta']}, leaf_cap "
-                      f"{WORKLOAD['leaf_cap']}), OpenMP over targets, {dt:.1f} s"}
+    tot_t, tot_i, reps = 0.0, 0, 0
+    nt = cloud.n
+    while tot_t < budget_s and reps < 20:
+        dt, inter = oracle_sample(cloud, nt, nthreads, seed=reps)
+        tot_t += dt
+        tot_i += inter
+        reps += 1
+        if reps == 1 and dt > budget_s:
+            break
+    return {"value": tot_i / tot_t, "unit": UNIT, "cores": nthreads, "kind": "oracle",
+            "sample": f"FP64 serial-tree oracle, {reps} x (tree build over all {cloud.n} "
+                      f"particles + walk of all {nt} targets, theta {WORKLOAD['theta']}, "
+                      f"leaf_cap {WORKLOAD['leaf_cap']}), OpenMP over targets, {tot_t:.1f} s"}
 
 
 def run_reference(args):
@@ -292,7 +299,7 @@ def run_gpu(args):
                 "frac": (achieved / peak) if achieved else None,
                 "traffic": traffic, "kernel": "k_walk_fp32c",
                 "peak_basis": f"FP32 pipe: {nsm} SMs x 128 lanes x 2 flop x {peak_mhz:.0f} MHz "
-                              "(max SM clock); flops = 20 per direct pair + 86 per multipole",
+                              "(max SM clock); flops = 20 per direct pair + 64 per multipole",
                 "walk_ms_per_launch": walk_ms / max(walk_n, 1), "walk_launches": walk_n,
                 "walk_share_of_step": walk_ms / ms if ms > 0 else None}
 

@@ -492,13 +492,6 @@ __device__ __forceinline__ void finish_box(const double* a, const double z[3],
                                      __dmul_rn(ez, ez)));
 }
 
-__device__ __forceinline__ double warp_sum(double v)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-
 __global__ void k_clear_children(Tree t)
 {
     int total = *t.nnodes * 8;
@@ -506,23 +499,23 @@ __global__ void k_clear_children(Tree t)
         t.child8[i] = -1;
 }
 
-// One warp per box.  A leaf sums its particles (lanes stride the key-ordered
-// range, coalesced); a twig is finished by the warp whose child completes the
-// twig's particle count (arrival counter), which gathers the eight child slots
-// in lanes 0-7 and shifts each child's moments to the twig's centre.  Results
-// do not depend on which warp finishes a twig.
+// One thread per box.  A leaf sums its particles about its geometric centre;
+// a twig is finished by the thread whose child completes the twig's particle
+// count (arrival counter): it reads the eight child slots in octant order and
+// shifts each child's moments to the twig's centre.  The arithmetic of a box
+// does not depend on which thread finishes it.  FP64 throughput is scarce on
+// this part, so the work per box is kept to one thread's worth of FP64 operations.
 __global__ void __launch_bounds__(256)
 k_moments(const double* __restrict__ x, const double* __restrict__ y,
           const double* __restrict__ z, const int8_t* __restrict__ sp,
           const double* __restrict__ qsp, const Cube* __restrict__ cube, Tree t,
           float4* __restrict__ src32, int want_f32)
 {
-    const int lane = threadIdx.x & 31;
-    const int nw = gridDim.x * (blockDim.x >> 5);
     const int nn = *t.nnodes;
     const Cube cb = *cube;
     const double q0 = qsp[0], q1 = qsp[1];
-    for (int node = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); node < nn; node += nw) {
+    for (int node = blockIdx.x * blockDim.x + threadIdx.x; node < nn;
+         node += gridDim.x * blockDim.x) {
         const int dl = t.depth_leaf[node];
         if (!(dl & 256)) continue;
         const int4 inf = t.info[node];
@@ -531,7 +524,7 @@ k_moments(const double* __restrict__ x, const double* __restrict__ y,
         double a[14];
 #pragma unroll
         for (int k = 0; k < 14; ++k) a[k] = 0.0;
-        for (int j = inf.x + lane; j < inf.y; j += 32) {
+        for (int j = inf.x; j < inf.y; ++j) {
             double qj = sp[j] ? q1 : q0;
             double aq = fabs(qj);
             double yv[3] = {x[j] - zc[0], y[j] - zc[1], z[j] - zc[2]};
@@ -542,24 +535,21 @@ k_moments(const double* __restrict__ x, const double* __restrict__ y,
                 a[2 + k] += aq * yv[k];
                 a[5 + k] += qj * yv[k];
             }
-            a[8] += qj * yv[0] * yv[0];
-            a[9] += qj * yv[0] * yv[1];
-            a[10] += qj * yv[0] * yv[2];
-            a[11] += qj * yv[1] * yv[1];
-            a[12] += qj * yv[1] * yv[2];
+            double qy0 = qj * yv[0], qy1 = qj * yv[1];
+            a[8] += qy0 * yv[0];
+            a[9] += qy0 * yv[1];
+            a[10] += qy0 * yv[2];
+            a[11] += qy1 * yv[1];
+            a[12] += qy1 * yv[2];
             a[13] += qj * yv[2] * yv[2];
         }
-#pragma unroll
-        for (int k = 0; k < 14; ++k) a[k] = warp_sum(a[k]);
         double rec[kMom];
         finish_box(a, zc, rec);
-        if (lane == 0) {
-            double* m = t.mom + (size_t)node * kMom;
+        double* m = t.mom + (size_t)node * kMom;
 #pragma unroll
-            for (int k = 0; k < kMom; ++k) m[k] = rec[k];
-        }
+        for (int k = 0; k < kMom; ++k) m[k] = rec[k];
         if (want_f32)
-            for (int j = inf.x + lane; j < inf.y; j += 32) {
+            for (int j = inf.x; j < inf.y; ++j) {
                 double qj = sp[j] ? q1 : q0;
                 src32[j] = make_float4((float)(x[j] - rec[MC]), (float)(y[j] - rec[MC + 1]),
                                        (float)(z[j] - rec[MC + 2]), (float)qj);
@@ -571,53 +561,49 @@ k_moments(const double* __restrict__ x, const double* __restrict__ y,
             if (p < 0) break;
             const int4 pin = t.info[p];
             const int pc = pin.y - pin.x;
-            int last = 0;
-            if (lane == 0) {
-                __threadfence();
-                int old = atomicAdd(&t.arrive[p], cnt);
-                last = old + cnt == pc;
-            }
-            if (!__shfl_sync(0xffffffffu, last, 0)) break;
+            __threadfence();
+            const int old = atomicAdd(&t.arrive[p], cnt);
+            if (old + cnt != pc) break;
             __threadfence();
             const int pd = t.depth_leaf[p] & 255;
             double zp[3], ps;
             box_centre(cb, t.cell[p], pd, zp, &ps);
+            const int4 c03 = *reinterpret_cast<const int4*>(t.child8 + (size_t)p * 8);
+            const int4 c47 = *reinterpret_cast<const int4*>(t.child8 + (size_t)p * 8 + 4);
+            const int chs[8] = {c03.x, c03.y, c03.z, c03.w, c47.x, c47.y, c47.z, c47.w};
 #pragma unroll
             for (int k = 0; k < 14; ++k) a[k] = 0.0;
-            if (lane < 8) {
-                const int ch = t.child8[(size_t)p * 8 + lane];
-                if (ch >= 0) {
-                    const double* cm = t.mom + (size_t)ch * kMom;
-                    double S0k = __ldcg(cm + MS0), Mk = __ldcg(cm + MM);
-                    double e[3], dk[3], qk[6];
-                    for (int k = 0; k < 3; ++k) {
-                        e[k] = __ldcg(cm + MC + k) - zp[k];
-                        dk[k] = __ldcg(cm + MD + k);
-                    }
-                    for (int k = 0; k < 6; ++k) qk[k] = __ldcg(cm + MQ + k);
-                    a[0] = S0k;
-                    a[1] = Mk;
-                    for (int k = 0; k < 3; ++k) {
-                        a[2 + k] = S0k * e[k];
-                        a[5 + k] = dk[k] + Mk * e[k];
-                    }
-                    // Q_k + D_k e^T + e D_k^T + M_k e e^T
-                    a[8] = qk[0] + 2.0 * dk[0] * e[0] + Mk * e[0] * e[0];
-                    a[9] = qk[1] + dk[0] * e[1] + e[0] * dk[1] + Mk * e[0] * e[1];
-                    a[10] = qk[2] + dk[0] * e[2] + e[0] * dk[2] + Mk * e[0] * e[2];
-                    a[11] = qk[3] + 2.0 * dk[1] * e[1] + Mk * e[1] * e[1];
-                    a[12] = qk[4] + dk[1] * e[2] + e[1] * dk[2] + Mk * e[1] * e[2];
-                    a[13] = qk[5] + 2.0 * dk[2] * e[2] + Mk * e[2] * e[2];
+#pragma unroll 1
+            for (int o = 0; o < 8; ++o) {
+                const int ch = chs[o];
+                if (ch < 0) continue;
+                const double* cm = t.mom + (size_t)ch * kMom;
+                double S0k = __ldcg(cm + MS0), Mk = __ldcg(cm + MM);
+                double e[3], dk[3], qk[6];
+                for (int k = 0; k < 3; ++k) {
+                    e[k] = __ldcg(cm + MC + k) - zp[k];
+                    dk[k] = __ldcg(cm + MD + k);
                 }
+                for (int k = 0; k < 6; ++k) qk[k] = __ldcg(cm + MQ + k);
+                a[0] += S0k;
+                a[1] += Mk;
+                for (int k = 0; k < 3; ++k) {
+                    a[2 + k] += S0k * e[k];
+                    a[5 + k] += dk[k] + Mk * e[k];
+                }
+                // Q_k + D_k e^T + e D_k^T + M_k e e^T
+                double me0 = Mk * e[0], me1 = Mk * e[1], me2 = Mk * e[2];
+                a[8] += qk[0] + (2.0 * dk[0] + me0) * e[0];
+                a[9] += qk[1] + dk[0] * e[1] + (dk[1] + me0) * e[0];
+                a[10] += qk[2] + dk[0] * e[2] + (dk[2] + me0) * e[0];
+                a[11] += qk[3] + (2.0 * dk[1] + me1) * e[1];
+                a[12] += qk[4] + dk[1] * e[2] + (dk[2] + me1) * e[1];
+                a[13] += qk[5] + (2.0 * dk[2] + me2) * e[2];
             }
-#pragma unroll
-            for (int k = 0; k < 14; ++k) a[k] = warp_sum(a[k]);
             finish_box(a, zp, rec);
-            if (lane == 0) {
-                double* m = t.mom + (size_t)p * kMom;
+            double* pm = t.mom + (size_t)p * kMom;
 #pragma unroll
-                for (int k = 0; k < kMom; ++k) m[k] = rec[k];
-            }
+            for (int k = 0; k < kMom; ++k) pm[k] = rec[k];
             cur = p;
             cnt = pc;
         }
@@ -701,7 +687,9 @@ void launch_moments(const double* x, const double* y, const double* z, const int
                     int want_f32, cudaStream_t s)
 {
     count_launch(1);
-    k_moments<<<8 * 152, 256, 0, s>>>(x, y, z, sp, qsp, cube, t, src32, want_f32);
+    int blocks = (n + 255) / 256;
+    if (blocks > 4 * 152) blocks = 4 * 152;
+    k_moments<<<blocks > 0 ? blocks : 1, 256, 0, s>>>(x, y, z, sp, qsp, cube, t, src32, want_f32);
 }
 
 }  // namespace ucp

@@ -8,10 +8,11 @@
 // per-target criterion is evaluated per lane; the warp descends into a box
 // when any lane opens it, and a lane that accepted an ancestor sits out until
 // the walk passes that ancestor's subtree (pre-order array with skip index
-// "next", no stack).  The walk writes (box, lane mask) entries into per-warp
-// interaction lists in shared memory; full lists are evaluated in bulk, so the
-// multipole and pair loops run without divergence.  Each lane sums its own
-// target in a fixed order, so results do not depend on scheduling.
+// "next", no stack).  Lanes that accept a box evaluate its expansion on the
+// spot, reusing R = x_t - c and |R|^2 from the criterion; opened leaves go
+// into a per-warp list in shared memory as (leaf, lane mask) and are summed in
+// bulk, so the pair loop is warp-uniform.  Each lane sums its own target in a
+// fixed order, so results do not depend on scheduling.
 #include "ucp_internal.cuh"
 
 #include <math.h>
@@ -22,13 +23,12 @@ namespace {
 
 constexpr int kWalkThreads = 128;
 constexpr int kWalkWarps = kWalkThreads / 32;
-constexpr int kList = 64;
+constexpr int kList = 64;      // opened leaves buffered per warp
+constexpr int kM2PBatch = 32;  // multipoles summed in FP32 before a compensated add
 
-struct WarpLists {
-    int m2p_node[kList];
-    unsigned int m2p_mask[kList];
-    int p2p_node[kList];
-    unsigned int p2p_mask[kList];
+struct WarpList {
+    int leaf[kList];
+    unsigned int mask[kList];
 };
 
 __device__ __forceinline__ int next_chunk(int* work, int lane)
@@ -38,42 +38,80 @@ __device__ __forceinline__ int next_chunk(int* work, int lane)
     return __shfl_sync(0xffffffffu, c, 0);
 }
 
-// ------------------------------------------------------------------ FP64
-// Field of a box's expansion at R = x_t - c (softened kernel g = (R^2+eps^2)^-1/2):
-//   E = M R g^3 - D g^3 + 3 (D.R) R g^5 - 3 (Q R) g^5 + 15/2 (R.Q.R) R g^7 - 3/2 tr(Q) R g^5
-//   phi = M g + (D.R) g^3 + 1/2 (3 R.Q.R g^5 - tr(Q) g^3)
-__device__ __forceinline__ void m2p_fp64(const double* __restrict__ m, double rx, double ry,
-                                         double rz, double eps2, double& ex, double& ey,
-                                         double& ez, double& ph)
+// Error-free sum (Knuth's TwoSum) folded into a running correction.
+__device__ __forceinline__ void two_sum_acc(float& s, float& c, float v)
 {
-    double M = m[MM];
-    double Dx = m[MD], Dy = m[MD + 1], Dz = m[MD + 2];
-    double Qxx = m[MQ], Qxy = m[MQ + 1], Qxz = m[MQ + 2], Qyy = m[MQ + 3], Qyz = m[MQ + 4],
-           Qzz = m[MQ + 5];
-    double r2 = rx * rx + ry * ry + rz * rz + eps2;
+    float t = s + v;
+    float bp = t - s;
+    float ap = t - bp;
+    c += (s - ap) + (v - bp);
+    s = t;
+}
+
+// ------------------------------------------------------------------ FP64
+// Expansion of a box at R = x_t - c, r2 = R.R + eps^2, g = r2^-1/2, u = g^2:
+//   phi = g (M + u (D.R - tr(Q)/2 + (3/2) u R.Q.R))
+//   E   = g^3 (M + 3u (D.R - tr(Q)/2 + (5/2) u R.Q.R)) R - g^3 (D + 3u Q R)
+// (the Taylor expansion of the softened kernel through second order, with the
+// terms of each power of u collected).
+template <class T>
+__device__ __forceinline__ void m2p(T rx, T ry, T rz, T r2, T M, T Dx, T Dy, T Dz, T Qxx, T Qxy,
+                                    T Qxz, T Qyy, T Qyz, T Qzz, T& ex, T& ey, T& ez, T& ph);
+
+template <>
+__device__ __forceinline__ void m2p<double>(double rx, double ry, double rz, double r2, double M,
+                                            double Dx, double Dy, double Dz, double Qxx,
+                                            double Qxy, double Qxz, double Qyy, double Qyz,
+                                            double Qzz, double& ex, double& ey, double& ez,
+                                            double& ph)
+{
     double g = rsqrt(r2);
-    double g2 = g * g;
-    double g3 = g * g2, g5 = g3 * g2, g7 = g5 * g2;
-    double DR = Dx * rx + Dy * ry + Dz * rz;
+    double u = g * g;
+    double g3 = g * u;
     double QRx = Qxx * rx + Qxy * ry + Qxz * rz;
     double QRy = Qxy * rx + Qyy * ry + Qyz * rz;
     double QRz = Qxz * rx + Qyz * ry + Qzz * rz;
     double RQR = rx * QRx + ry * QRy + rz * QRz;
-    double trQ = Qxx + Qyy + Qzz;
-    double a = M * g3 + 3.0 * DR * g5 + 7.5 * RQR * g7 - 1.5 * trQ * g5;
-    double b = 3.0 * g5;
-    ex += a * rx - Dx * g3 - b * QRx;
-    ey += a * ry - Dy * g3 - b * QRy;
-    ez += a * rz - Dz * g3 - b * QRz;
-    ph += M * g + DR * g3 + 0.5 * (3.0 * RQR * g5 - trQ * g3);
+    double w = Dx * rx + Dy * ry + Dz * rz - 0.5 * (Qxx + Qyy + Qzz);
+    double h = u * RQR;
+    ph += g * (M + u * (w + 1.5 * h));
+    double s3 = 3.0 * u;
+    double aa = g3 * (M + s3 * (w + 2.5 * h));
+    ex += aa * rx - g3 * (Dx + s3 * QRx);
+    ey += aa * ry - g3 * (Dy + s3 * QRy);
+    ez += aa * rz - g3 * (Dz + s3 * QRz);
+}
+
+template <>
+__device__ __forceinline__ void m2p<float>(float rx, float ry, float rz, float r2, float M, float Dx,
+                                           float Dy, float Dz, float Qxx, float Qxy, float Qxz,
+                                           float Qyy, float Qyz, float Qzz, float& ex, float& ey,
+                                           float& ez, float& ph)
+{
+    float g = rsqrtf(r2);
+    float u = g * g;
+    float g3 = g * u;
+    float QRx = fmaf(Qxx, rx, fmaf(Qxy, ry, Qxz * rz));
+    float QRy = fmaf(Qxy, rx, fmaf(Qyy, ry, Qyz * rz));
+    float QRz = fmaf(Qxz, rx, fmaf(Qyz, ry, Qzz * rz));
+    float RQR = fmaf(rx, QRx, fmaf(ry, QRy, rz * QRz));
+    float w = fmaf(Dx, rx, fmaf(Dy, ry, fmaf(Dz, rz, -0.5f * (Qxx + Qyy + Qzz))));
+    float h = u * RQR;
+    ph = fmaf(g, fmaf(u, fmaf(1.5f, h, w), M), ph);
+    float s3 = 3.f * u;
+    float aa = g3 * fmaf(s3, fmaf(2.5f, h, w), M);
+    float mg3 = -g3;
+    ex = fmaf(mg3, fmaf(s3, QRx, Dx), fmaf(aa, rx, ex));
+    ey = fmaf(mg3, fmaf(s3, QRy, Dy), fmaf(aa, ry, ey));
+    ez = fmaf(mg3, fmaf(s3, QRz, Dz), fmaf(aa, rz, ez));
 }
 
 __global__ void __launch_bounds__(kWalkThreads)
 k_walk_fp64(WalkArgs a)
 {
-    __shared__ WarpLists L[kWalkWarps];
+    __shared__ WarpList L[kWalkWarps];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    WarpLists& lst = L[w];
+    WarpList& lst = L[w];
     const int nn = *a.t.nnodes;
     const double q0 = a.qsp[0], q1 = a.qsp[1];
     const double* __restrict__ mom = a.t.mom;
@@ -93,21 +131,13 @@ k_walk_fp64(WalkArgs a)
         double ex = 0.0, ey = 0.0, ez = 0.0, ph = 0.0;
         int np = 0, nm = 0;
         int skip = valid ? 0 : 0x7fffffff;
-        int nml = 0, npl = 0;
+        int npl = 0;
 
         auto flush = [&]() {
             __syncwarp();
-            for (int e = 0; e < nml; ++e) {
-                int nd = lst.m2p_node[e];
-                if ((lst.m2p_mask[e] >> lane) & 1u) {
-                    const double* m = mom + (size_t)nd * kMom;
-                    m2p_fp64(m, xt - m[0], yt - m[1], zt - m[2], a.eps2, ex, ey, ez, ph);
-                    ++nm;
-                }
-            }
             for (int e = 0; e < npl; ++e) {
-                int nd = lst.p2p_node[e];
-                if ((lst.p2p_mask[e] >> lane) & 1u) {
+                int nd = lst.leaf[e];
+                if ((lst.mask[e] >> lane) & 1u) {
                     int4 inf = info[nd];
                     for (int j = inf.x; j < inf.y; ++j) {
                         if (j == t) continue;
@@ -124,7 +154,6 @@ k_walk_fp64(WalkArgs a)
                     }
                 }
             }
-            nml = 0;
             npl = 0;
             __syncwarp();
         };
@@ -143,31 +172,27 @@ k_walk_fp64(WalkArgs a)
                                   __dmul_rn(dz, dz));
             const bool acc = active && (m[MR2] < d2);
             const bool opn = active && !acc;
-            const unsigned int am = __ballot_sync(0xffffffffu, acc);
             const unsigned int om = __ballot_sync(0xffffffffu, opn);
-            if (am) {
-                if (lane == 0) {
-                    lst.m2p_node[nml] = node;
-                    lst.m2p_mask[nml] = am;
-                }
-                ++nml;
-            }
+            int next = inf.z;
             if (om) {
                 if (leaf) {
                     if (lane == 0) {
-                        lst.p2p_node[npl] = node;
-                        lst.p2p_mask[npl] = om;
+                        lst.leaf[npl] = node;
+                        lst.mask[npl] = om;
                     }
                     ++npl;
-                    node = inf.z;
                 } else {
                     if (acc) skip = inf.z;
-                    node = node + 1;
+                    next = node + 1;
                 }
-            } else {
-                node = inf.z;
             }
-            if (nml == kList || npl == kList) flush();
+            if (acc) {
+                m2p<double>(dx, dy, dz, d2 + a.eps2, m[MM], m[MD], m[MD + 1], m[MD + 2], m[MQ],
+                            m[MQ + 1], m[MQ + 2], m[MQ + 3], m[MQ + 4], m[MQ + 5], ex, ey, ez, ph);
+                ++nm;
+            }
+            node = next;
+            if (npl == kList) flush();
         }
         flush();
 
@@ -195,22 +220,12 @@ k_walk_fp64(WalkArgs a)
 }
 
 // ------------------------------------------------------------------ FP32C
-// Error-free sum (Knuth's TwoSum): s + e == a + b exactly.
-__device__ __forceinline__ void two_sum_acc(float& s, float& c, float v)
-{
-    float t = s + v;
-    float bp = t - s;
-    float ap = t - bp;
-    c += (s - ap) + (v - bp);
-    s = t;
-}
-
 __global__ void __launch_bounds__(kWalkThreads)
 k_walk_fp32c(WalkArgs a)
 {
-    __shared__ WarpLists L[kWalkWarps];
+    __shared__ WarpList L[kWalkWarps];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    WarpLists& lst = L[w];
+    WarpList& lst = L[w];
     const int nn = *a.t.nnodes;
     const double q0 = a.qsp[0], q1 = a.qsp[1];
     const float4* __restrict__ F = a.t.f32;
@@ -229,51 +244,26 @@ k_walk_fp32c(WalkArgs a)
             xh = (float)X; yh = (float)Y; zh = (float)Z;
             xl = (float)(X - (double)xh); yl = (float)(Y - (double)yh); zl = (float)(Z - (double)zh);
         }
-        // compensated accumulators (sum, correction) for E and phi
+        // compensated totals (sum, correction) and the current multipole batch
         float sx = 0.f, sy = 0.f, sz = 0.f, sp = 0.f, cx = 0.f, cy = 0.f, cz = 0.f, cp = 0.f;
-        int np = 0, nm = 0;
+        float bx = 0.f, by = 0.f, bz = 0.f, bp = 0.f;
+        int np = 0, nm = 0, nb = 0;
         int skip = valid ? 0 : 0x7fffffff;
-        int nml = 0, npl = 0;
+        int npl = 0;
 
-        auto flush = [&]() {
-            __syncwarp();
-            float bx = 0.f, by = 0.f, bz = 0.f, bp = 0.f;
-            for (int e = 0; e < nml; ++e) {
-                int nd = lst.m2p_node[e];
-                if ((lst.m2p_mask[e] >> lane) & 1u) {
-                    const float4* r = F + (size_t)nd * kF32;
-                    float4 A = r[0], B = r[1], C = r[2], D = r[3], E = r[4];
-                    float rx = (xh - A.x) + (xl - B.x);
-                    float ry = (yh - A.y) + (yl - B.y);
-                    float rz = (zh - A.z) + (zl - B.z);
-                    float M = C.z, Dx = C.w, Dy = D.x, Dz = D.y;
-                    float Qxx = D.z, Qxy = D.w, Qxz = E.x, Qyy = E.y, Qyz = E.z, Qzz = E.w;
-                    float r2 = fmaf(rx, rx, fmaf(ry, ry, fmaf(rz, rz, eps2)));
-                    float g = rsqrtf(r2);
-                    float g2 = g * g;
-                    float g3 = g * g2, g5 = g3 * g2, g7 = g5 * g2;
-                    float DR = fmaf(Dx, rx, fmaf(Dy, ry, Dz * rz));
-                    float QRx = fmaf(Qxx, rx, fmaf(Qxy, ry, Qxz * rz));
-                    float QRy = fmaf(Qxy, rx, fmaf(Qyy, ry, Qyz * rz));
-                    float QRz = fmaf(Qxz, rx, fmaf(Qyz, ry, Qzz * rz));
-                    float RQR = fmaf(rx, QRx, fmaf(ry, QRy, rz * QRz));
-                    float trQ = Qxx + Qyy + Qzz;
-                    float aa = fmaf(M, g3, fmaf(3.f * DR, g5, fmaf(7.5f * RQR, g7, -1.5f * trQ * g5)));
-                    float b = 3.f * g5;
-                    bx += fmaf(aa, rx, -fmaf(Dx, g3, b * QRx));
-                    by += fmaf(aa, ry, -fmaf(Dy, g3, b * QRy));
-                    bz += fmaf(aa, rz, -fmaf(Dz, g3, b * QRz));
-                    bp += fmaf(M, g, fmaf(DR, g3, 0.5f * fmaf(3.f * RQR, g5, -trQ * g3)));
-                    ++nm;
-                }
-            }
+        auto fold_batch = [&]() {
             two_sum_acc(sx, cx, bx);
             two_sum_acc(sy, cy, by);
             two_sum_acc(sz, cz, bz);
             two_sum_acc(sp, cp, bp);
+            bx = by = bz = bp = 0.f;
+        };
+
+        auto flush = [&]() {
+            __syncwarp();
             for (int e = 0; e < npl; ++e) {
-                int nd = lst.p2p_node[e];
-                if ((lst.p2p_mask[e] >> lane) & 1u) {
+                int nd = lst.leaf[e];
+                if ((lst.mask[e] >> lane) & 1u) {
                     const float4* r = F + (size_t)nd * kF32;
                     float4 A = r[0], B = r[1], C = r[2];
                     float rx = (xh - A.x) + (xl - B.x);
@@ -281,6 +271,7 @@ k_walk_fp32c(WalkArgs a)
                     float rz = (zh - A.z) + (zl - B.z);
                     int jb = __float_as_int(C.x), je = __float_as_int(C.y);
                     float px = 0.f, py = 0.f, pz = 0.f, pp = 0.f;
+#pragma unroll 4
                     for (int j = jb; j < je; ++j) {
                         float4 s = __ldg(S + j);
                         float dx = rx - s.x, dy = ry - s.y, dz = rz - s.z;
@@ -300,7 +291,6 @@ k_walk_fp32c(WalkArgs a)
                     two_sum_acc(sp, cp, pp);
                 }
             }
-            nml = 0;
             npl = 0;
             __syncwarp();
         };
@@ -308,7 +298,7 @@ k_walk_fp32c(WalkArgs a)
         int node = 0;
         while (node < nn) {
             const float4* r = F + (size_t)node * kF32;
-            const float4 A = r[0], B = r[1], C = r[2];
+            const float4 A = r[0], B = r[1], C = r[2], D = r[3], E = r[4];
             const int nxt = __float_as_int(B.w);
             const bool leaf = __float_as_int(C.y) >= 0;
             const bool active = node >= skip;
@@ -330,33 +320,34 @@ k_walk_fp32c(WalkArgs a)
                 acc = m[MR2] < dd;
             }
             const bool opn = active && !acc;
-            const unsigned int am = __ballot_sync(0xffffffffu, acc);
             const unsigned int om = __ballot_sync(0xffffffffu, opn);
-            if (am) {
-                if (lane == 0) {
-                    lst.m2p_node[nml] = node;
-                    lst.m2p_mask[nml] = am;
-                }
-                ++nml;
-            }
+            int next = nxt;
             if (om) {
                 if (leaf) {
                     if (lane == 0) {
-                        lst.p2p_node[npl] = node;
-                        lst.p2p_mask[npl] = om;
+                        lst.leaf[npl] = node;
+                        lst.mask[npl] = om;
                     }
                     ++npl;
-                    node = nxt;
                 } else {
                     if (acc) skip = nxt;
-                    node = node + 1;
+                    next = node + 1;
                 }
-            } else {
-                node = nxt;
             }
-            if (nml == kList || npl == kList) flush();
+            if (acc) {
+                m2p<float>(rx, ry, rz, d2 + eps2, C.z, C.w, D.x, D.y, D.z, D.w, E.x, E.y, E.z,
+                           E.w, bx, by, bz, bp);
+                ++nm;
+                if (++nb == kM2PBatch) {
+                    fold_batch();
+                    nb = 0;
+                }
+            }
+            node = next;
+            if (npl == kList) flush();
         }
         flush();
+        fold_batch();
 
         if (valid) {
             const int s = a.sp[t];
