@@ -594,10 +594,10 @@ k_moments(const double* __restrict__ x, const double* __restrict__ y,
                 // Q_k + D_k e^T + e D_k^T + M_k e e^T
                 double me0 = Mk * e[0], me1 = Mk * e[1], me2 = Mk * e[2];
                 a[8] += qk[0] + (2.0 * dk[0] + me0) * e[0];
-                a[9] += qk[1] + dk[0] * e[1] + (dk[1] + me0) * e[0];
-                a[10] += qk[2] + dk[0] * e[2] + (dk[2] + me0) * e[0];
+                a[9] += qk[1] + dk[0] * e[1] + (dk[1] + me1) * e[0];
+                a[10] += qk[2] + dk[0] * e[2] + (dk[2] + me2) * e[0];
                 a[11] += qk[3] + (2.0 * dk[1] + me1) * e[1];
-                a[12] += qk[4] + dk[1] * e[2] + (dk[2] + me1) * e[1];
+                a[12] += qk[4] + dk[1] * e[2] + (dk[2] + me2) * e[1];
                 a[13] += qk[5] + (2.0 * dk[2] + me2) * e[2];
             }
             finish_box(a, zp, rec);
