@@ -142,6 +142,30 @@ int ucp_profile_read(ucp_ctx* ctx, double* walk_ms, int64_t* walk_launches);
 const char* ucp_strerror(int code);
 const char* ucp_last_error(ucp_ctx* ctx);
 
+/* Enclosing cube without any allocation.  The paper has no counterpart: this
+ * is a service for callers that must not allocate GPU memory at this point --
+ * for example code running while a CUDA graph is being captured (where
+ * cudaMalloc is not allowed), code that works under a fixed device-memory
+ * budget owned by another allocator, or real-time loops that forbid
+ * allocation after start-up.  It computes the same cube as ucp_tree_build
+ * (centre = (min + max) / 2 per axis, side = largest extent * (1 + 2^-20),
+ * side 1 when all particles coincide) from pos (device, N x 3 double) into
+ * cube_out (device, 4 doubles {centre x, y, z, side}), enqueued on stream
+ * (cudaStream_t, NULL = legacy stream); it returns after enqueueing.
+ * It calls no cudaMalloc or cudaFree: its per-tile partial results live in a
+ * fixed array in the library's device memory (UCP_STATIC_MAX_N /
+ * UCP_STATIC_TILE slots of 6 doubles, 48 KB, present on every GPU that loads
+ * the library until the process exits).  N outside [1, UCP_STATIC_MAX_N]
+ * returns UCP_EINVAL; a failed CUDA call returns UCP_ECUDA.
+ * The first call on a device looks up that array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture.  All calls share the one array and each call overwrites the slots
+ * it uses, so calls that may run at the same time on the GPU (different
+ * streams without ordering between them) race and must be serialised. */
+#define UCP_STATIC_TILE 2048
+#define UCP_STATIC_MAX_N (1024 * UCP_STATIC_TILE)
+int ucp_root_cube_static(const double* pos, int64_t n, double* cube_out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif
