@@ -548,12 +548,19 @@ k_moments(const double* __restrict__ x, const double* __restrict__ y,
         double* m = t.mom + (size_t)node * kMom;
 #pragma unroll
         for (int k = 0; k < kMom; ++k) m[k] = rec[k];
-        if (want_f32)
+        if (want_f32) {
+            // paired layout: src32[2p] = {nx_2p, nx_2p+1, ny_2p, ny_2p+1},
+            // src32[2p+1] = {nz_2p, nz_2p+1, q_2p, q_2p+1}, n = c_leaf - x
+            float* f = reinterpret_cast<float*>(src32);
             for (int j = inf.x; j < inf.y; ++j) {
                 double qj = sp[j] ? q1 : q0;
-                src32[j] = make_float4((float)(x[j] - rec[MC]), (float)(y[j] - rec[MC + 1]),
-                                       (float)(z[j] - rec[MC + 2]), (float)qj);
+                size_t b = (size_t)(j >> 1) * 8 + (j & 1);
+                f[b] = (float)(rec[MC] - x[j]);
+                f[b + 2] = (float)(rec[MC + 1] - y[j]);
+                f[b + 4] = (float)(rec[MC + 2] - z[j]);
+                f[b + 6] = (float)qj;
             }
+        }
 
         int cur = node, cnt = inf.y - inf.x;
         while (true) {

@@ -80,7 +80,8 @@ struct WalkArgs {
     const int8_t* sp;
     const double* qsp;      // charge per species (device, 2)
     const double* msp;      // mass per species (device, 2)
-    const float4* src32;    // FP32C source offsets and charges (key order)
+    const float4* src32;    // FP32C sources, pairs of particles: {nx0, nx1, ny0, ny1},
+                            // {nz0, nz1, q0, q1} with n = c_leaf - x (key order)
     Tree t;
     const int* targets;     // key-order slots of the targets, or NULL = all
     int ntargets;

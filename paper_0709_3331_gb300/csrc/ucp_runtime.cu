@@ -326,8 +326,12 @@ int ucp_create(ucp_ctx** out, const ucp_params* p)
         (rc = dalloc(c, &c->t.arrive, cz)) || (rc = dalloc(c, &c->t.child8, cz * 8)))
         return bail(rc);
     if (c->precision == UCP_FP32C) {
-        if ((rc = dalloc(c, &c->t.f32, cz * kF32)) || (rc = dalloc(c, &c->src32, n)))
+        // sources in pairs: 2 float4 per pair of particles (padded to an even count)
+        if ((rc = dalloc(c, &c->t.f32, cz * kF32)) || (rc = dalloc(c, &c->src32, n + 1)))
             return bail(rc);
+        // the pad slot of an odd count is read (masked) by the pair loop: keep it finite
+        if (cudaMemsetAsync(c->src32, 0, sizeof(float4) * (n + 1), c->s) != cudaSuccess)
+            return bail(UCP_ECUDA);
     }
     if ((rc = dalloc(c, &c->cube, 1))) return bail(rc);
     c->bbox_nblk = (int)((n + 2047) / 2048);

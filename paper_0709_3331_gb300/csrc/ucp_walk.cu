@@ -24,7 +24,8 @@ namespace {
 constexpr int kWalkThreads = 128;
 constexpr int kWalkWarps = kWalkThreads / 32;
 constexpr int kList = 64;      // opened leaves buffered per warp
-constexpr int kM2PBatch = 32;  // multipoles summed in FP32 before a compensated add
+constexpr int kM2PBatch = 32;  // visits whose multipoles are summed in FP32 before a
+                               // compensated add (a power of two)
 
 struct WarpList {
     int leaf[kList];
@@ -220,7 +221,7 @@ k_walk_fp64(WalkArgs a)
 }
 
 // ------------------------------------------------------------------ FP32C
-__global__ void __launch_bounds__(kWalkThreads)
+__global__ void __launch_bounds__(kWalkThreads, 7)
 k_walk_fp32c(WalkArgs a)
 {
     __shared__ WarpList L[kWalkWarps];
@@ -247,7 +248,7 @@ k_walk_fp32c(WalkArgs a)
         // compensated totals (sum, correction) and the current multipole batch
         float sx = 0.f, sy = 0.f, sz = 0.f, sp = 0.f, cx = 0.f, cy = 0.f, cz = 0.f, cp = 0.f;
         float bx = 0.f, by = 0.f, bz = 0.f, bp = 0.f;
-        int np = 0, nm = 0, nb = 0;
+        int np = 0, nm = 0, vis = 0;
         int skip = valid ? 0 : 0x7fffffff;
         int npl = 0;
 
@@ -270,25 +271,34 @@ k_walk_fp32c(WalkArgs a)
                     float ry = (yh - A.y) + (yl - B.y);
                     float rz = (zh - A.z) + (zl - B.z);
                     int jb = __float_as_int(C.x), je = __float_as_int(C.y);
-                    float px = 0.f, py = 0.f, pz = 0.f, pp = 0.f;
-#pragma unroll 4
-                    for (int j = jb; j < je; ++j) {
-                        float4 s = __ldg(S + j);
-                        float dx = rx - s.x, dy = ry - s.y, dz = rz - s.z;
-                        float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
-                        float ri = (j == t) ? 0.f : rsqrtf(r2);
-                        float qi = s.w * ri;
-                        float qr3 = qi * ri * ri;
-                        px = fmaf(qr3, dx, px);
-                        py = fmaf(qr3, dy, py);
-                        pz = fmaf(qr3, dz, pz);
-                        pp += qi;
+                    // sources in pairs {x_2p, x_2p+1, y.., y..}, {z.., z.., q.., q..} as
+                    // offsets c_leaf - x_j; a pair member outside [jb, je) or equal to
+                    // the target gets a zero inverse distance
+                    const float2 rx2 = make_float2(rx, rx), ry2 = make_float2(ry, ry),
+                                 rz2 = make_float2(rz, rz), e2 = make_float2(eps2, eps2);
+                    float2 px = make_float2(0.f, 0.f), py = px, pz = px, pp = px;
+#pragma unroll 2
+                    for (int j = jb & ~1; j < je; j += 2) {
+                        const float4 P = __ldg(S + j), Q = __ldg(S + j + 1);
+                        float2 dx = __fadd2_rn(rx2, make_float2(P.x, P.y));
+                        float2 dy = __fadd2_rn(ry2, make_float2(P.z, P.w));
+                        float2 dz = __fadd2_rn(rz2, make_float2(Q.x, Q.y));
+                        float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __ffma2_rn(dz, dz, e2)));
+                        const bool ok0 = j >= jb && j != t;
+                        const bool ok1 = j + 1 < je && j + 1 != t;
+                        float2 ri = make_float2(ok0 ? rsqrtf(r2.x) : 0.f, ok1 ? rsqrtf(r2.y) : 0.f);
+                        float2 qi = __fmul2_rn(make_float2(Q.z, Q.w), ri);
+                        float2 qr3 = __fmul2_rn(__fmul2_rn(qi, ri), ri);
+                        px = __ffma2_rn(qr3, dx, px);
+                        py = __ffma2_rn(qr3, dy, py);
+                        pz = __ffma2_rn(qr3, dz, pz);
+                        pp = __fadd2_rn(pp, qi);
                     }
                     np += (je - jb) - ((t >= jb && t < je) ? 1 : 0);
-                    two_sum_acc(sx, cx, px);
-                    two_sum_acc(sy, cy, py);
-                    two_sum_acc(sz, cz, pz);
-                    two_sum_acc(sp, cp, pp);
+                    two_sum_acc(sx, cx, px.x + px.y);
+                    two_sum_acc(sy, cy, py.x + py.y);
+                    two_sum_acc(sz, cz, pz.x + pz.y);
+                    two_sum_acc(sp, cp, pp.x + pp.y);
                 }
             }
             npl = 0;
@@ -338,11 +348,8 @@ k_walk_fp32c(WalkArgs a)
                 m2p<float>(rx, ry, rz, d2 + eps2, C.z, C.w, D.x, D.y, D.z, D.w, E.x, E.y, E.z,
                            E.w, bx, by, bz, bp);
                 ++nm;
-                if (++nb == kM2PBatch) {
-                    fold_batch();
-                    nb = 0;
-                }
             }
+            if ((++vis & (kM2PBatch - 1)) == 0) fold_batch();
             node = next;
             if (npl == kList) flush();
         }
