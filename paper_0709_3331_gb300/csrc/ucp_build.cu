@@ -427,8 +427,9 @@ __global__ void k_topo_emit(const unsigned long long* __restrict__ K, int n, int
         t.info[node] = make_int4(i, e, nx, parent);
         t.depth_leaf[node] = d | (leaf ? 256 : 0);
         t.cell[node] = pre;
-        t.arrive[node] = 0;
         if (parent >= 0) t.child8[(size_t)parent * 8 + (int)(pre & 7ull)] = node;
+        if (leaf) t.leaf_list[atomicAdd(&t.count[kMaxDepth + 1], 1)] = node;
+        else t.twig_list[t.twig_off[d] + atomicAdd(&t.count[d], 1)] = node;
         parent = node;
         ++node;
         dmax = d;
@@ -472,7 +473,8 @@ __device__ __forceinline__ void finish_box(const double* a, const double z[3],
 {
     double S0 = a[0], M = a[1];
     double e[3];
-    for (int k = 0; k < 3; ++k) e[k] = S0 > 0.0 ? a[2 + k] / S0 : 0.0;
+    const double inv = S0 > 0.0 ? 1.0 / S0 : 0.0;
+    for (int k = 0; k < 3; ++k) e[k] = a[2 + k] * inv;
     double d[3];
     for (int k = 0; k < 3; ++k) d[k] = a[5 + k];
     m[MC + 0] = z[0] + e[0];
@@ -499,25 +501,20 @@ __global__ void k_clear_children(Tree t)
         t.child8[i] = -1;
 }
 
-// One thread per box.  A leaf sums its particles about its geometric centre;
-// a twig is finished by the thread whose child completes the twig's particle
-// count (arrival counter): it reads the eight child slots in octant order and
-// shifts each child's moments to the twig's centre.  The arithmetic of a box
-// does not depend on which thread finishes it.  FP64 throughput is scarce on
-// this part, so the work per box is kept to one thread's worth of FP64 operations.
+// Moments of every leaf from its particles, one thread per leaf, summed about
+// the leaf's geometric centre in key order.
 __global__ void __launch_bounds__(256)
-k_moments(const double* __restrict__ x, const double* __restrict__ y,
-          const double* __restrict__ z, const int8_t* __restrict__ sp,
-          const double* __restrict__ qsp, const Cube* __restrict__ cube, Tree t,
-          float4* __restrict__ src32, int want_f32)
+k_moments_leaves(const double* __restrict__ x, const double* __restrict__ y,
+                 const double* __restrict__ z, const int8_t* __restrict__ sp,
+                 const double* __restrict__ qsp, const Cube* __restrict__ cube, Tree t,
+                 float4* __restrict__ src32, int want_f32)
 {
-    const int nn = *t.nnodes;
+    const int nl = t.count[kMaxDepth + 1];
     const Cube cb = *cube;
     const double q0 = qsp[0], q1 = qsp[1];
-    for (int node = blockIdx.x * blockDim.x + threadIdx.x; node < nn;
-         node += gridDim.x * blockDim.x) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nl; i += gridDim.x * blockDim.x) {
+        const int node = t.leaf_list[i];
         const int dl = t.depth_leaf[node];
-        if (!(dl & 256)) continue;
         const int4 inf = t.info[node];
         double zc[3], side;
         box_centre(cb, t.cell[node], dl & 255, zc, &side);
@@ -561,59 +558,61 @@ k_moments(const double* __restrict__ x, const double* __restrict__ y,
                 f[b + 6] = (float)qj;
             }
         }
+    }
+}
 
-        int cur = node, cnt = inf.y - inf.x;
-        while (true) {
-            const int p = t.info[cur].w;
-            if (p < 0) break;
-            const int4 pin = t.info[p];
-            const int pc = pin.y - pin.x;
-            __threadfence();
-            const int old = atomicAdd(&t.arrive[p], cnt);
-            if (old + cnt != pc) break;
-            __threadfence();
-            const int pd = t.depth_leaf[p] & 255;
-            double zp[3], ps;
-            box_centre(cb, t.cell[p], pd, zp, &ps);
-            const int4 c03 = *reinterpret_cast<const int4*>(t.child8 + (size_t)p * 8);
-            const int4 c47 = *reinterpret_cast<const int4*>(t.child8 + (size_t)p * 8 + 4);
-            const int chs[8] = {c03.x, c03.y, c03.z, c03.w, c47.x, c47.y, c47.z, c47.w};
+// Moments of the twigs of one depth, one thread per twig: the eight child slots
+// in octant order, each child's moments shifted to the twig's geometric centre.
+// Depths are processed from the deepest up, one launch each, so every child is
+// complete; the arithmetic of a twig does not depend on the schedule.
+__global__ void __launch_bounds__(256)
+k_moments_twigs(const Cube* __restrict__ cube, Tree t, int d)
+{
+    const int nt = t.count[d];
+    const Cube cb = *cube;
+    const int* __restrict__ list = t.twig_list + t.twig_off[d];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nt; i += gridDim.x * blockDim.x) {
+        const int p = list[i];
+        double zp[3], ps;
+        box_centre(cb, t.cell[p], d, zp, &ps);
+        const int4 c03 = *reinterpret_cast<const int4*>(t.child8 + (size_t)p * 8);
+        const int4 c47 = *reinterpret_cast<const int4*>(t.child8 + (size_t)p * 8 + 4);
+        const int chs[8] = {c03.x, c03.y, c03.z, c03.w, c47.x, c47.y, c47.z, c47.w};
+        double a[14];
 #pragma unroll
-            for (int k = 0; k < 14; ++k) a[k] = 0.0;
+        for (int k = 0; k < 14; ++k) a[k] = 0.0;
 #pragma unroll 1
-            for (int o = 0; o < 8; ++o) {
-                const int ch = chs[o];
-                if (ch < 0) continue;
-                const double* cm = t.mom + (size_t)ch * kMom;
-                double S0k = __ldcg(cm + MS0), Mk = __ldcg(cm + MM);
-                double e[3], dk[3], qk[6];
-                for (int k = 0; k < 3; ++k) {
-                    e[k] = __ldcg(cm + MC + k) - zp[k];
-                    dk[k] = __ldcg(cm + MD + k);
-                }
-                for (int k = 0; k < 6; ++k) qk[k] = __ldcg(cm + MQ + k);
-                a[0] += S0k;
-                a[1] += Mk;
-                for (int k = 0; k < 3; ++k) {
-                    a[2 + k] += S0k * e[k];
-                    a[5 + k] += dk[k] + Mk * e[k];
-                }
-                // Q_k + D_k e^T + e D_k^T + M_k e e^T
-                double me0 = Mk * e[0], me1 = Mk * e[1], me2 = Mk * e[2];
-                a[8] += qk[0] + (2.0 * dk[0] + me0) * e[0];
-                a[9] += qk[1] + dk[0] * e[1] + (dk[1] + me1) * e[0];
-                a[10] += qk[2] + dk[0] * e[2] + (dk[2] + me2) * e[0];
-                a[11] += qk[3] + (2.0 * dk[1] + me1) * e[1];
-                a[12] += qk[4] + dk[1] * e[2] + (dk[2] + me2) * e[1];
-                a[13] += qk[5] + (2.0 * dk[2] + me2) * e[2];
+        for (int o = 0; o < 8; ++o) {
+            const int ch = chs[o];
+            if (ch < 0) continue;
+            const double* cm = t.mom + (size_t)ch * kMom;
+            double S0k = cm[MS0], Mk = cm[MM];
+            double e[3], dk[3], qk[6];
+            for (int k = 0; k < 3; ++k) {
+                e[k] = cm[MC + k] - zp[k];
+                dk[k] = cm[MD + k];
             }
-            finish_box(a, zp, rec);
-            double* pm = t.mom + (size_t)p * kMom;
-#pragma unroll
-            for (int k = 0; k < kMom; ++k) pm[k] = rec[k];
-            cur = p;
-            cnt = pc;
+            for (int k = 0; k < 6; ++k) qk[k] = cm[MQ + k];
+            a[0] += S0k;
+            a[1] += Mk;
+            for (int k = 0; k < 3; ++k) {
+                a[2 + k] += S0k * e[k];
+                a[5 + k] += dk[k] + Mk * e[k];
+            }
+            // Q_k + D_k e^T + e D_k^T + M_k e e^T
+            double me0 = Mk * e[0], me1 = Mk * e[1], me2 = Mk * e[2];
+            a[8] += qk[0] + (2.0 * dk[0] + me0) * e[0];
+            a[9] += qk[1] + dk[0] * e[1] + (dk[1] + me1) * e[0];
+            a[10] += qk[2] + dk[0] * e[2] + (dk[2] + me2) * e[0];
+            a[11] += qk[3] + (2.0 * dk[1] + me1) * e[1];
+            a[12] += qk[4] + dk[1] * e[2] + (dk[2] + me2) * e[1];
+            a[13] += qk[5] + (2.0 * dk[2] + me2) * e[2];
         }
+        double rec[kMom];
+        finish_box(a, zp, rec);
+        double* pm = t.mom + (size_t)p * kMom;
+#pragma unroll
+        for (int k = 0; k < kMom; ++k) pm[k] = rec[k];
     }
 }
 
@@ -683,6 +682,7 @@ void launch_topology(const unsigned long long* key, int n, int leaf_cap, int* po
 {
     count_launch(3);
     cudaMemsetAsync(t.maxdepth, 0, sizeof(int), s);
+    cudaMemsetAsync(t.count, 0, sizeof(int) * (kMaxDepth + 2), s);
     k_topo_count<<<(n + 255) / 256, 256, 0, s>>>(key, n, leaf_cap, pos_cnt);
     launch_scan(pos_cnt, pos_off, n, scan_part, t.nnodes, s);
     k_clear_children<<<2 * 152, 256, 0, s>>>(t);
@@ -693,10 +693,17 @@ void launch_moments(const double* x, const double* y, const double* z, const int
                     const double* qsp, int n, const Cube* cube, Tree t, float4* src32,
                     int want_f32, cudaStream_t s)
 {
-    count_launch(1);
+    count_launch(1 + kMaxDepth);
     int blocks = (n + 255) / 256;
     if (blocks > 4 * 152) blocks = 4 * 152;
-    k_moments<<<blocks > 0 ? blocks : 1, 256, 0, s>>>(x, y, z, sp, qsp, cube, t, src32, want_f32);
+    k_moments_leaves<<<blocks > 0 ? blocks : 1, 256, 0, s>>>(x, y, z, sp, qsp, cube, t, src32,
+                                                            want_f32);
+    for (int d = kMaxDepth - 1; d >= 0; --d) {
+        int cap = t.twig_off[d + 1] - t.twig_off[d];
+        int b = (cap + 255) / 256;
+        if (b > 2 * 152) b = 2 * 152;
+        k_moments_twigs<<<b > 0 ? b : 1, 256, 0, s>>>(cube, t, d);
+    }
 }
 
 }  // namespace ucp

@@ -40,8 +40,11 @@ struct Tree {
     unsigned long long* cell;// key prefix of the box at its depth
     double* mom;             // kMom doubles per box
     float4* f32;             // kF32 float4 per box
-    int* arrive;             // bottom-up arrival counters (particles)
     int* child8;             // 8 child slots per box (octant order), -1 = empty
+    int* leaf_list;          // the leaves, any order
+    int* twig_list;          // the twigs of depth d at twig_off[d] .. + count[d]
+    int* count;              // count[d] twigs of depth d (d <= 20), count[kMaxDepth + 1] leaves
+    int twig_off[kMaxDepth + 2];
 };
 
 struct Cube {                // enclosing cube: centre, side, lower corner, 2^21 / side

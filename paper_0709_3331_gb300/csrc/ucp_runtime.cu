@@ -323,8 +323,20 @@ int ucp_create(ucp_ctx** out, const ucp_params* p)
     if ((rc = dalloc(c, &c->t.nnodes, 1)) || (rc = dalloc(c, &c->t.maxdepth, 1)) ||
         (rc = dalloc(c, &c->t.info, cz)) || (rc = dalloc(c, &c->t.depth_leaf, cz)) ||
         (rc = dalloc(c, &c->t.cell, cz)) || (rc = dalloc(c, &c->t.mom, cz * kMom)) ||
-        (rc = dalloc(c, &c->t.arrive, cz)) || (rc = dalloc(c, &c->t.child8, cz * 8)))
+        (rc = dalloc(c, &c->t.child8, cz * 8)) || (rc = dalloc(c, &c->t.leaf_list, cz)) ||
+        (rc = dalloc(c, &c->t.count, kMaxDepth + 2)))
         return bail(rc);
+    {
+        // twigs of depth d: at most min(8^d, n / (leaf_cap + 1)); none at the depth cap
+        int64_t off = 0, pow8 = 1, twigs = c->n / (c->leaf_cap + 1);
+        for (int d = 0; d <= kMaxDepth + 1; ++d) {
+            c->t.twig_off[d] = (int)off;
+            int64_t lim = d < kMaxDepth ? (pow8 < twigs ? pow8 : twigs) : 0;
+            off += lim;
+            if (pow8 < ((int64_t)1 << 40)) pow8 *= 8;
+        }
+        if ((rc = dalloc(c, &c->t.twig_list, (size_t)(off > 0 ? off : 1)))) return bail(rc);
+    }
     if (c->precision == UCP_FP32C) {
         // sources in pairs: 2 float4 per pair of particles (padded to an even count)
         if ((rc = dalloc(c, &c->t.f32, cz * kF32)) || (rc = dalloc(c, &c->src32, n + 1)))
