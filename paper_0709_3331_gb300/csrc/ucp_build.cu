@@ -616,6 +616,148 @@ k_moments_twigs(const Cube* __restrict__ cube, Tree t, int d)
     }
 }
 
+// ---- FP32 moments (FP32C contexts).  Offsets from a box's geometric centre z
+// are at most one box side, so they are formed in FP64 once and summed in FP32;
+// the expansion centre is c = z + e exactly as stored (FP64), and D, Q are taken
+// about that same point.  Compact per-box record mom32 = {e xyz, S0, M, D xyz,
+// Q xx xy xz yy yz zz, 0, 0} feeds the twig combine.
+__device__ __forceinline__ void finish_box_f32(const float* a, const double z[3], float* m32,
+                                               double* __restrict__ m64)
+{
+    float S0 = a[0], M = a[1];
+    float inv = S0 > 0.f ? 1.f / S0 : 0.f;
+    float e[3] = {a[2] * inv, a[3] * inv, a[4] * inv};
+    float d[3];
+    for (int k = 0; k < 3; ++k) d[k] = fmaf(-M, e[k], a[5 + k]);
+    const int ia[6] = {0, 0, 0, 1, 1, 2}, ib[6] = {0, 1, 2, 1, 2, 2};
+    float q[6];
+    for (int k = 0; k < 6; ++k)
+        q[k] = a[8 + k] - a[5 + ia[k]] * e[ib[k]] - e[ia[k]] * a[5 + ib[k]] +
+               M * e[ia[k]] * e[ib[k]];
+    m32[0] = e[0];
+    m32[1] = e[1];
+    m32[2] = e[2];
+    m32[3] = S0;
+    m32[4] = M;
+    for (int k = 0; k < 3; ++k) m32[5 + k] = d[k];
+    for (int k = 0; k < 6; ++k) m32[8 + k] = q[k];
+    m32[14] = 0.f;
+    m32[15] = 0.f;
+    for (int k = 0; k < 3; ++k) m64[MC + k] = z[k] + (double)e[k];
+    m64[MM] = M;
+    for (int k = 0; k < 3; ++k) m64[MD + k] = d[k];
+    for (int k = 0; k < 6; ++k) m64[MQ + k] = q[k];
+    m64[MS0] = S0;
+    m64[MDELTA] = sqrtf(fmaf(e[0], e[0], fmaf(e[1], e[1], e[2] * e[2])));
+}
+
+__global__ void __launch_bounds__(256)
+k_moments_leaves_f32(const double* __restrict__ x, const double* __restrict__ y,
+                     const double* __restrict__ z, const int8_t* __restrict__ sp,
+                     const double* __restrict__ qsp, const Cube* __restrict__ cube, Tree t,
+                     float4* __restrict__ src32)
+{
+    const int nl = t.count[kMaxDepth + 1];
+    const Cube cb = *cube;
+    const float q0 = (float)qsp[0], q1 = (float)qsp[1];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nl; i += gridDim.x * blockDim.x) {
+        const int node = t.leaf_list[i];
+        const int dl = t.depth_leaf[node];
+        const int4 inf = t.info[node];
+        double zc[3], side;
+        box_centre(cb, t.cell[node], dl & 255, zc, &side);
+        float a[14];
+#pragma unroll
+        for (int k = 0; k < 14; ++k) a[k] = 0.f;
+        for (int j = inf.x; j < inf.y; ++j) {
+            float qj = sp[j] ? q1 : q0;
+            float aq = fabsf(qj);
+            float yv[3] = {(float)(x[j] - zc[0]), (float)(y[j] - zc[1]), (float)(z[j] - zc[2])};
+            a[0] += aq;
+            a[1] += qj;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                a[2 + k] = fmaf(aq, yv[k], a[2 + k]);
+                a[5 + k] = fmaf(qj, yv[k], a[5 + k]);
+            }
+            float qy0 = qj * yv[0], qy1 = qj * yv[1];
+            a[8] = fmaf(qy0, yv[0], a[8]);
+            a[9] = fmaf(qy0, yv[1], a[9]);
+            a[10] = fmaf(qy0, yv[2], a[10]);
+            a[11] = fmaf(qy1, yv[1], a[11]);
+            a[12] = fmaf(qy1, yv[2], a[12]);
+            a[13] = fmaf(qj * yv[2], yv[2], a[13]);
+        }
+        float m32[16];
+        double* m = t.mom + (size_t)node * kMom;
+        finish_box_f32(a, zc, m32, m);
+        float4* r32 = reinterpret_cast<float4*>(t.mom32 + (size_t)node * 16);
+        for (int k = 0; k < 4; ++k)
+            r32[k] = make_float4(m32[4 * k], m32[4 * k + 1], m32[4 * k + 2], m32[4 * k + 3]);
+        // paired sources: src32[2p] = {nx_2p, nx_2p+1, ny_2p, ny_2p+1},
+        // src32[2p+1] = {nz_2p, nz_2p+1, q_2p, q_2p+1}, n = c_leaf - x
+        const double cx = m[MC], cy = m[MC + 1], cz = m[MC + 2];
+        float* f = reinterpret_cast<float*>(src32);
+        for (int j = inf.x; j < inf.y; ++j) {
+            size_t b = (size_t)(j >> 1) * 8 + (j & 1);
+            f[b] = (float)(cx - x[j]);
+            f[b + 2] = (float)(cy - y[j]);
+            f[b + 4] = (float)(cz - z[j]);
+            f[b + 6] = sp[j] ? q1 : q0;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256)
+k_moments_twigs_f32(const Cube* __restrict__ cube, Tree t, int d)
+{
+    const int nt = t.count[d];
+    const Cube cb = *cube;
+    const int* __restrict__ list = t.twig_list + t.twig_off[d];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nt; i += gridDim.x * blockDim.x) {
+        const int p = list[i];
+        double zp[3], ps;
+        box_centre(cb, t.cell[p], d, zp, &ps);
+        const int4 c03 = *reinterpret_cast<const int4*>(t.child8 + (size_t)p * 8);
+        const int4 c47 = *reinterpret_cast<const int4*>(t.child8 + (size_t)p * 8 + 4);
+        const int chs[8] = {c03.x, c03.y, c03.z, c03.w, c47.x, c47.y, c47.z, c47.w};
+        float a[14];
+#pragma unroll
+        for (int k = 0; k < 14; ++k) a[k] = 0.f;
+#pragma unroll 1
+        for (int o = 0; o < 8; ++o) {
+            const int ch = chs[o];
+            if (ch < 0) continue;
+            const double* cm = t.mom + (size_t)ch * kMom;
+            const float4* r32 = reinterpret_cast<const float4*>(t.mom32 + (size_t)ch * 16);
+            const float4 R1 = r32[1], R2 = r32[2], R3 = r32[3];
+            const float S0k = r32[0].w, Mk = R1.x;
+            const float dk[3] = {R1.y, R1.z, R1.w};
+            const float qk[6] = {R2.x, R2.y, R2.z, R2.w, R3.x, R3.y};
+            float e[3];
+            for (int k = 0; k < 3; ++k) e[k] = (float)(cm[MC + k] - zp[k]);
+            a[0] += S0k;
+            a[1] += Mk;
+            for (int k = 0; k < 3; ++k) {
+                a[2 + k] = fmaf(S0k, e[k], a[2 + k]);
+                a[5 + k] += fmaf(Mk, e[k], dk[k]);
+            }
+            float me0 = Mk * e[0], me1 = Mk * e[1], me2 = Mk * e[2];
+            a[8] += qk[0] + (2.f * dk[0] + me0) * e[0];
+            a[9] += qk[1] + dk[0] * e[1] + (dk[1] + me1) * e[0];
+            a[10] += qk[2] + dk[0] * e[2] + (dk[2] + me2) * e[0];
+            a[11] += qk[3] + (2.f * dk[1] + me1) * e[1];
+            a[12] += qk[4] + dk[1] * e[2] + (dk[2] + me2) * e[1];
+            a[13] += qk[5] + (2.f * dk[2] + me2) * e[2];
+        }
+        float m32[16];
+        finish_box_f32(a, zp, m32, t.mom + (size_t)p * kMom);
+        float4* w32 = reinterpret_cast<float4*>(t.mom32 + (size_t)p * 16);
+        for (int k = 0; k < 4; ++k)
+            w32[k] = make_float4(m32[4 * k], m32[4 * k + 1], m32[4 * k + 2], m32[4 * k + 3]);
+    }
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------- launchers
@@ -696,13 +838,18 @@ void launch_moments(const double* x, const double* y, const double* z, const int
     count_launch(1 + kMaxDepth);
     int blocks = (n + 255) / 256;
     if (blocks > 4 * 152) blocks = 4 * 152;
-    k_moments_leaves<<<blocks > 0 ? blocks : 1, 256, 0, s>>>(x, y, z, sp, qsp, cube, t, src32,
-                                                            want_f32);
+    if (blocks < 1) blocks = 1;
+    if (want_f32)
+        k_moments_leaves_f32<<<blocks, 256, 0, s>>>(x, y, z, sp, qsp, cube, t, src32);
+    else
+        k_moments_leaves<<<blocks, 256, 0, s>>>(x, y, z, sp, qsp, cube, t, src32, 0);
     for (int d = kMaxDepth - 1; d >= 0; --d) {
         int cap = t.twig_off[d + 1] - t.twig_off[d];
         int b = (cap + 255) / 256;
         if (b > 2 * 152) b = 2 * 152;
-        k_moments_twigs<<<b > 0 ? b : 1, 256, 0, s>>>(cube, t, d);
+        if (b < 1) b = 1;
+        if (want_f32) k_moments_twigs_f32<<<b, 256, 0, s>>>(cube, t, d);
+        else k_moments_twigs<<<b, 256, 0, s>>>(cube, t, d);
     }
 }
 

@@ -40,6 +40,7 @@ struct Tree {
     unsigned long long* cell;// key prefix of the box at its depth
     double* mom;             // kMom doubles per box
     float4* f32;             // kF32 float4 per box
+    float* mom32;            // FP32C contexts: 16 floats per box {e xyz, S0, M, D, Q, 0, 0}
     int* child8;             // 8 child slots per box (octant order), -1 = empty
     int* leaf_list;          // the leaves, any order
     int* twig_list;          // the twigs of depth d at twig_off[d] .. + count[d]

@@ -339,7 +339,8 @@ int ucp_create(ucp_ctx** out, const ucp_params* p)
     }
     if (c->precision == UCP_FP32C) {
         // sources in pairs: 2 float4 per pair of particles (padded to an even count)
-        if ((rc = dalloc(c, &c->t.f32, cz * kF32)) || (rc = dalloc(c, &c->src32, n + 1)))
+        if ((rc = dalloc(c, &c->t.f32, cz * kF32)) || (rc = dalloc(c, &c->src32, n + 1)) ||
+            (rc = dalloc(c, &c->t.mom32, cz * 16)))
             return bail(rc);
         // the pad slot of an odd count is read (masked) by the pair loop: keep it finite
         if (cudaMemsetAsync(c->src32, 0, sizeof(float4) * (n + 1), c->s) != cudaSuccess)

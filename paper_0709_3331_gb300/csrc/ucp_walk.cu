@@ -221,7 +221,7 @@ k_walk_fp64(WalkArgs a)
 }
 
 // ------------------------------------------------------------------ FP32C
-__global__ void __launch_bounds__(kWalkThreads, 8)
+__global__ void __launch_bounds__(kWalkThreads, 7)
 k_walk_fp32c(WalkArgs a)
 {
     __shared__ WarpList L[kWalkWarps];
@@ -277,7 +277,7 @@ k_walk_fp32c(WalkArgs a)
                     const float2 rx2 = make_float2(rx, rx), ry2 = make_float2(ry, ry),
                                  rz2 = make_float2(rz, rz), e2 = make_float2(eps2, eps2);
                     float2 px = make_float2(0.f, 0.f), py = px, pz = px, pp = px;
-#pragma unroll 1
+#pragma unroll 2
                     for (int j = jb & ~1; j < je; j += 2) {
                         const float4 P = __ldg(S + j), Q = __ldg(S + j + 1);
                         float2 dx = __fadd2_rn(rx2, make_float2(P.x, P.y));
