@@ -106,6 +106,20 @@ class Clocks:
                 "samples": len(rows)}
 
 
+def reduce_over_ranks(ms, count, device="cpu"):
+    """Replicas run independently; the job's time is the slowest rank's and its
+    work is the sum over ranks (weak scaling).  Single process: unchanged."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(ms), float(count)
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    c = torch.tensor([float(count)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(c, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(c.item())
+
+
 def git_rev():
     try:
         return subprocess.run(["git", "-C", ROOT, "rev-parse", "--short", "HEAD"],
@@ -278,14 +292,7 @@ def run_gpu(args):
     clocks = clk.stop()
     inter = int(st[0] + st[1])
     launches = int(st[6])
-    if ws > 1:
-        t = torch.tensor([ms, float(inter)], dtype=torch.float64, device=dev)
-        tmax = t.clone()
-        dist.all_reduce(tmax[:1], op=dist.ReduceOp.MAX)
-        dist.all_reduce(t[1:], op=dist.ReduceOp.SUM)
-        ms_all, inter_all = float(tmax[0]), float(t[1])
-    else:
-        ms_all, inter_all = ms, float(inter)
+    ms_all, inter_all = reduce_over_ranks(ms, inter, dev)
     value = inter_all / (ms_all / 1e3)
     pst = W["n"] * W["k"] * args.steps * ws / (ms_all / 1e3)
 
@@ -380,13 +387,8 @@ def run_e2e(c, W, args, ws, dev, flush, Context, UCP_FP32C):
     torch.cuda.synchronize()
     e_t = time.perf_counter() - e0
     st_h = ctx_h.stats(reset=True)
-    e_val = float(st_h[0] + st_h[1]) / e_t
-    if ws > 1:
-        t = torch.tensor([e_t, float(st_h[0] + st_h[1])], dtype=torch.float64, device=dev)
-        tm = t.clone()
-        dist.all_reduce(tm[:1], op=dist.ReduceOp.MAX)
-        dist.all_reduce(t[1:], op=dist.ReduceOp.SUM)
-        e_val = float(t[1]) / float(tm[0])
+    e_t_all, e_cnt = reduce_over_ranks(e_t, float(st_h[0] + st_h[1]), dev)
+    e_val = e_cnt / e_t_all
     e2e = {"value": e_val, "unit": UNIT,
            "h2d_bytes_per_step": int(c.pos.nbytes + c.vel.nbytes + c.species.nbytes),
            "d2h_bytes_per_step": int(c.pos.nbytes + c.vel.nbytes + 6 * 8),
