@@ -133,6 +133,12 @@ int ucp_get_tree(ucp_ctx* ctx, int64_t* nnodes, int64_t cap, int32_t* topo,
                  int8_t* is_leaf, double* geom);
 int ucp_get_counts(ucp_ctx* ctx, int32_t* p2p, int32_t* m2p, int on_device);
 
+/* Failure-path self-test: runs one pass of the key sort as a lone block whose
+ * predecessor never publishes, so its bounded wait runs out.  Returns
+ * UCP_ETIMEOUT when the wait gave up and raised the error flag as it must (the
+ * flag is cleared again and the context stays usable), UCP_OK if it did not. */
+int ucp_selftest_wait_timeout(ucp_ctx* ctx);
+
 /* Kernel timing: when enabled, the walk kernels are bracketed by CUDA events
  * on the context's stream; read returns {total ms, launches} of the walk since
  * the last read (synchronises the stream). */

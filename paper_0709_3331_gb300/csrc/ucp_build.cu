@@ -218,41 +218,68 @@ constexpr int kSortWarps = kSortThreads / 32;
 constexpr int kSortChunks = 8;                              // 32-key chunks per warp
 constexpr int kSortTile = kSortThreads * kSortChunks;       // 2048 keys per block
 constexpr int kRadix = 256;
+constexpr int kSortSpinLimit = 1 << 20;  // polls of a predecessor's word before giving up
 
+// Digit histograms of all eight passes in one read of the keys.
 __global__ void __launch_bounds__(kSortThreads)
-k_radix_hist(const unsigned long long* __restrict__ key, int n, int shift,
-             unsigned int* __restrict__ hist)
+k_sort_hist_all(const unsigned long long* __restrict__ key, int n, unsigned int* __restrict__ ghist)
 {
-    __shared__ unsigned int cnt[kRadix];
-    cnt[threadIdx.x] = 0;
+    __shared__ unsigned int h[8][kRadix];
+    for (int i = threadIdx.x; i < 8 * kRadix; i += kSortThreads) (&h[0][0])[i] = 0;
     __syncthreads();
-    int base = blockIdx.x * kSortTile;
+    for (int i = blockIdx.x * kSortThreads + threadIdx.x; i < n; i += gridDim.x * kSortThreads) {
+        unsigned long long k = key[i];
 #pragma unroll
-    for (int k = 0; k < kSortChunks; ++k) {
-        int i = base + k * kSortThreads + threadIdx.x;
-        if (i < n) atomicAdd(&cnt[(unsigned int)(key[i] >> shift) & 0xffu], 1u);
+        for (int p = 0; p < 8; ++p) atomicAdd(&h[p][(unsigned int)(k >> (8 * p)) & 0xffu], 1u);
     }
     __syncthreads();
-    hist[threadIdx.x * gridDim.x + blockIdx.x] = cnt[threadIdx.x];
+    for (int i = threadIdx.x; i < 8 * kRadix; i += kSortThreads) {
+        unsigned int v = (&h[0][0])[i];
+        if (v) atomicAdd(&ghist[i], v);
+    }
 }
 
-// Stable scatter: warp w owns the contiguous sub-tile [w*256, w*256+256) of the
-// block's tile and ranks its keys chunk by chunk in order with match_any, so
-// equal digits keep their input order.
+// goff[p][d] = number of keys whose pass-p digit is below d.
+__global__ void __launch_bounds__(kRadix) k_sort_offsets(const unsigned int* __restrict__ ghist,
+                                                         unsigned int* __restrict__ goff)
+{
+    __shared__ int tot;
+    for (int p = 0; p < 8; ++p) {
+        int v = (int)ghist[p * kRadix + threadIdx.x];
+        goff[p * kRadix + threadIdx.x] = (unsigned int)block_excl_scan(v, &tot);
+    }
+}
+
+// One stable LSD pass in a single kernel (decoupled look-back).  A block takes
+// the next tile from a counter, ranks its keys stably (each warp owns a
+// contiguous quarter-tile and ranks it chunk by chunk with match_any), and
+// publishes its per-digit count; the digit offset of the tile is the sum of
+// the counts of all earlier tiles, read back through their published words
+// {epoch, flag (1 = count of the tile, 2 = inclusive prefix), value}.  A block
+// waits only on tiles taken before its own, whose blocks are running, and
+// every wait is bounded: past spin_limit polls it raises *err, keeps its keys
+// where they are and leaves (the host reports UCP_ETIMEOUT).
 __global__ void __launch_bounds__(kSortThreads)
-k_radix_scatter(const unsigned long long* __restrict__ kin, const unsigned int* __restrict__ vin,
-                unsigned long long* __restrict__ kout, unsigned int* __restrict__ vout, int n,
-                int shift, const unsigned int* __restrict__ off)
+k_onesweep(const unsigned long long* __restrict__ kin, const unsigned int* __restrict__ vin,
+           unsigned long long* __restrict__ kout, unsigned int* __restrict__ vout, int n,
+           int shift, const unsigned int* __restrict__ goff, unsigned long long* status,
+           int* tile_ctr, unsigned int epoch, int* err, int spin_limit)
 {
     __shared__ int cnt[kSortWarps][kRadix];
-    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    __shared__ int s_tile, s_fail;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (threadIdx.x == 0) {
+        s_tile = atomicAdd(tile_ctr, 1);
+        s_fail = 0;
+    }
     for (int d = lane; d < kRadix; d += 32) cnt[w][d] = 0;
-    __syncwarp();
-    int base = blockIdx.x * kSortTile + w * (kSortTile / kSortWarps);
+    __syncthreads();
+    const int tile = s_tile;
+    const int base = tile * kSortTile + w * (kSortTile / kSortWarps);
     unsigned long long kk[kSortChunks];
     unsigned int vv[kSortChunks];
     int dig[kSortChunks], rank[kSortChunks];
-    unsigned int lt = (1u << lane) - 1u;
+    const unsigned int lt = (1u << lane) - 1u;
 #pragma unroll
     for (int c = 0; c < kSortChunks; ++c) {
         int i = base + c * 32 + lane;
@@ -273,22 +300,48 @@ k_radix_scatter(const unsigned long long* __restrict__ kin, const unsigned int* 
         __syncwarp();
     }
     __syncthreads();
-    // exclusive scan over warps per digit, plus the block's global offset
     {
-        int d = threadIdx.x;  // kSortThreads == kRadix
-        unsigned int run = off[d * gridDim.x + blockIdx.x];
+        const int d = threadIdx.x;  // kSortThreads == kRadix
+        int total = 0;
         for (int ww = 0; ww < kSortWarps; ++ww) {
             int t = cnt[ww][d];
-            cnt[ww][d] = (int)run;
-            run += t;
+            cnt[ww][d] = total;
+            total += t;
         }
+        const unsigned long long tag = (unsigned long long)epoch << 34;
+        unsigned long long* mine = status + (size_t)tile * kRadix + d;
+        unsigned int prefix = 0;
+        if (tile > 0) {
+            atomicExch(mine, tag | (1ull << 32) | (unsigned int)total);
+            int j = tile - 1, spins = 0;
+            while (j >= 0) {
+                unsigned long long v = __ldcv(status + (size_t)j * kRadix + d);
+                unsigned int flag = (unsigned int)(v >> 32) & 3u;
+                if ((v >> 34) != (unsigned long long)epoch || flag == 0u) {
+                    if (++spins > spin_limit) {
+                        atomicOr(err, 1);
+                        s_fail = 1;
+                        break;
+                    }
+                    __nanosleep(64);
+                    continue;
+                }
+                prefix += (unsigned int)v;
+                if (flag == 2u) break;
+                --j;
+            }
+        }
+        atomicExch(mine, tag | (2ull << 32) | (prefix + (unsigned int)total));
+        const int off = (int)(goff[d] + prefix);
+        for (int ww = 0; ww < kSortWarps; ++ww) cnt[ww][d] += off;
     }
     __syncthreads();
+    const bool fail = s_fail != 0;
 #pragma unroll
     for (int c = 0; c < kSortChunks; ++c) {
         int i = base + c * 32 + lane;
         if (i < n) {
-            int p = cnt[w][dig[c]] + rank[c];
+            int p = fail ? i : cnt[w][dig[c]] + rank[c];
             kout[p] = kk[c];
             vout[p] = vv[c];
         }
@@ -407,8 +460,10 @@ __global__ void k_topo_emit(const unsigned long long* __restrict__ K, int n, int
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     int c = cnt[i];
+    // the capacity bounds the box count of sorted keys; clamp in case it ever did not
+    int nn = min(*t.nnodes, t.cap);
+    if (i == 0 && *t.nnodes > t.cap) *t.nnodes = t.cap;
     if (c == 0) return;
-    int nn = *t.nnodes;
     int d0 = first_depth(K, i);
     int node = off[i];
     int parent = -1;
@@ -566,10 +621,12 @@ k_moments_leaves(const double* __restrict__ x, const double* __restrict__ y,
 // Depths are processed from the deepest up, one launch each, so every child is
 // complete; the arithmetic of a twig does not depend on the schedule.
 __global__ void __launch_bounds__(256)
-k_moments_twigs(const Cube* __restrict__ cube, Tree t, int d)
+k_moments_twigs(const Cube* __restrict__ cube, Tree t, int d_hi, int d_lo)
 {
-    const int nt = t.count[d];
     const Cube cb = *cube;
+    // several depths in one launch only with a single block (barrier between depths)
+    for (int d = d_hi; d >= d_lo; --d) {
+    const int nt = t.count[d];
     const int* __restrict__ list = t.twig_list + t.twig_off[d];
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nt; i += gridDim.x * blockDim.x) {
         const int p = list[i];
@@ -613,6 +670,8 @@ k_moments_twigs(const Cube* __restrict__ cube, Tree t, int d)
         double* pm = t.mom + (size_t)p * kMom;
 #pragma unroll
         for (int k = 0; k < kMom; ++k) pm[k] = rec[k];
+    }
+    if (d > d_lo) __syncthreads();
     }
 }
 
@@ -709,10 +768,12 @@ k_moments_leaves_f32(const double* __restrict__ x, const double* __restrict__ y,
 }
 
 __global__ void __launch_bounds__(256)
-k_moments_twigs_f32(const Cube* __restrict__ cube, Tree t, int d)
+k_moments_twigs_f32(const Cube* __restrict__ cube, Tree t, int d_hi, int d_lo)
 {
-    const int nt = t.count[d];
     const Cube cb = *cube;
+    // several depths in one launch only with a single block (barrier between depths)
+    for (int d = d_hi; d >= d_lo; --d) {
+    const int nt = t.count[d];
     const int* __restrict__ list = t.twig_list + t.twig_off[d];
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nt; i += gridDim.x * blockDim.x) {
         const int p = list[i];
@@ -756,6 +817,8 @@ k_moments_twigs_f32(const Cube* __restrict__ cube, Tree t, int d)
         for (int k = 0; k < 4; ++k)
             w32[k] = make_float4(m32[4 * k], m32[4 * k + 1], m32[4 * k + 2], m32[4 * k + 3]);
     }
+    if (d > d_lo) __syncthreads();
+    }
 }
 
 }  // namespace
@@ -788,28 +851,55 @@ void launch_keys(const double* x, const double* y, const double* z, int n, const
     k_keys<<<(n + 255) / 256, 256, 0, s>>>(x, y, z, n, cube, key, val);
 }
 
-size_t sort_scratch_words(int n)
+size_t sort_test_words() { return 4 * (size_t)kSortTile; }
+
+size_t sort_status_words(int n)
 {
     int nb = (n + kSortTile - 1) / kSortTile;
-    return (size_t)kRadix * (size_t)(nb > 0 ? nb : 1);
+    return (size_t)8 * kRadix * (size_t)(nb > 0 ? nb : 1);
 }
 
 void launch_sort(unsigned long long* key[2], unsigned int* val[2], int n, SortScratch sc,
-                 const unsigned int* ids_in, cudaStream_t s)
+                 const unsigned int* ids_in, unsigned int epoch0, cudaStream_t s)
 {
-    count_launch(17);
-    int nb = (n + kSortTile - 1) / kSortTile;
+    count_launch(11);
+    const int nb = (n + kSortTile - 1) / kSortTile;
+    cudaMemsetAsync(sc.ghist, 0, sizeof(unsigned int) * (8 * kRadix + 8), s);  // + tile counters
+    int hb = (n + 4 * kSortThreads - 1) / (4 * kSortThreads);
+    if (hb > 2 * 152) hb = 2 * 152;
+    k_sort_hist_all<<<hb > 0 ? hb : 1, kSortThreads, 0, s>>>(key[0], n, sc.ghist);
+    k_sort_offsets<<<1, kRadix, 0, s>>>(sc.ghist, sc.goff);
+    int* tiles = reinterpret_cast<int*>(sc.ghist + 8 * kRadix);
     int cur = 0;
-    for (int shift = 0; shift < 64; shift += 8) {
-        k_radix_hist<<<nb, kSortThreads, 0, s>>>(key[cur], n, shift, sc.hist);
-        launch_scan((const int*)sc.hist, (int*)sc.hist, kRadix * nb, (int*)sc.hist_part, nullptr,
-                    s);
-        k_radix_scatter<<<nb, kSortThreads, 0, s>>>(key[cur], val[cur], key[cur ^ 1], val[cur ^ 1],
-                                                    n, shift, sc.hist);
+    for (int p = 0; p < 8; ++p) {
+        k_onesweep<<<nb, kSortThreads, 0, s>>>(key[cur], val[cur], key[cur ^ 1], val[cur ^ 1], n,
+                                               8 * p, sc.goff + p * kRadix,
+                                               sc.status + (size_t)p * nb * kRadix, tiles + p,
+                                               epoch0 + (unsigned int)p, sc.err, kSortSpinLimit);
         cur ^= 1;
     }
     // eight passes: the result is back in buffer 0
     k_tiefix<<<(n + 255) / 256, 256, 0, s>>>(key[0], val[0], ids_in, n);
+}
+
+int sort_selftest_timeout(SortScratch sc, cudaStream_t s)
+{
+    // a lone block that takes tile 1 while tile 0 never publishes: its bounded
+    // wait must run out, raise *err and leave the keys where they are
+    count_launch(1);
+    static const int one = 1;
+    int* tiles = reinterpret_cast<int*>(sc.ghist + 8 * kRadix);
+    if (cudaMemsetAsync(sc.status, 0, sizeof(unsigned long long) * 2 * kRadix, s) != cudaSuccess ||
+        cudaMemcpyAsync(tiles, &one, sizeof(int), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemsetAsync(sc.goff, 0, sizeof(unsigned int) * kRadix, s) != cudaSuccess ||
+        cudaMemsetAsync(sc.test_keys, 0, sizeof(unsigned long long) * 4 * kSortTile, s) != cudaSuccess ||
+        cudaMemsetAsync(sc.test_vals, 0, sizeof(unsigned int) * 4 * kSortTile, s) != cudaSuccess)
+        return -1;
+    // input: tiles 0-1 of the test buffers; output: tiles 2-3
+    k_onesweep<<<1, kSortThreads, 0, s>>>(sc.test_keys, sc.test_vals, sc.test_keys + 2 * kSortTile,
+                                          sc.test_vals + 2 * kSortTile, 2 * kSortTile, 0, sc.goff,
+                                          sc.status, tiles, 1u, sc.err, 2000);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
 void launch_tiefix(const unsigned long long* key, unsigned int* perm, const unsigned int* ids,
@@ -835,7 +925,7 @@ void launch_moments(const double* x, const double* y, const double* z, const int
                     const double* qsp, int n, const Cube* cube, Tree t, float4* src32,
                     int want_f32, cudaStream_t s)
 {
-    count_launch(1 + kMaxDepth);
+    count_launch(1 + 10);
     int blocks = (n + 255) / 256;
     if (blocks > 4 * 152) blocks = 4 * 152;
     if (blocks < 1) blocks = 1;
@@ -843,14 +933,20 @@ void launch_moments(const double* x, const double* y, const double* z, const int
         k_moments_leaves_f32<<<blocks, 256, 0, s>>>(x, y, z, sp, qsp, cube, t, src32);
     else
         k_moments_leaves<<<blocks, 256, 0, s>>>(x, y, z, sp, qsp, cube, t, src32, 0);
-    for (int d = kMaxDepth - 1; d >= 0; --d) {
+    // deep depths (usually empty) and the top depths (at most 8^4 twigs) each in
+    // one single-block launch; the middle depths one multi-block launch each
+    auto twigs = [&](int d_hi, int d_lo, int b) {
+        if (want_f32) k_moments_twigs_f32<<<b, 256, 0, s>>>(cube, t, d_hi, d_lo);
+        else k_moments_twigs<<<b, 256, 0, s>>>(cube, t, d_hi, d_lo);
+    };
+    twigs(kMaxDepth - 1, 13, 1);
+    for (int d = 12; d >= 5; --d) {
         int cap = t.twig_off[d + 1] - t.twig_off[d];
         int b = (cap + 255) / 256;
         if (b > 2 * 152) b = 2 * 152;
-        if (b < 1) b = 1;
-        if (want_f32) k_moments_twigs_f32<<<b, 256, 0, s>>>(cube, t, d);
-        else k_moments_twigs<<<b, 256, 0, s>>>(cube, t, d);
+        twigs(d, d, b < 1 ? 1 : b);
     }
+    twigs(4, 0, 1);
 }
 
 }  // namespace ucp

@@ -61,13 +61,18 @@ void launch_bbox(const double* x, const double* y, const double* z, int n, doubl
 void launch_keys(const double* x, const double* y, const double* z, int n, const Cube* cube,
                  unsigned long long* key, unsigned int* val, cudaStream_t s);
 struct SortScratch {
-    unsigned int* hist;      // 256 x nblocks
-    unsigned int* hist_part; // scan partials
-    int nblocks;
+    unsigned int* ghist;           // 8 x 256 digit counts, then 8 tile counters
+    unsigned int* goff;            // 8 x 256 digit offsets
+    unsigned long long* status;    // 8 passes x tiles x 256 published words
+    int* err;                      // raised by a wait that gave up
+    unsigned long long* test_keys; // 4 tiles, for the bounded-wait self-test
+    unsigned int* test_vals;
 };
-size_t sort_scratch_words(int n);
+size_t sort_status_words(int n);
+size_t sort_test_words();
 void launch_sort(unsigned long long* key[2], unsigned int* val[2], int n, SortScratch sc,
-                 const unsigned int* ids_in, cudaStream_t s);
+                 const unsigned int* ids_in, unsigned int epoch0, cudaStream_t s);
+int sort_selftest_timeout(SortScratch sc, cudaStream_t s);
 void launch_tiefix(const unsigned long long* key, unsigned int* perm, const unsigned int* ids,
                    int n, cudaStream_t s);
 void launch_topology(const unsigned long long* key, int n, int leaf_cap, int* pos_cnt,

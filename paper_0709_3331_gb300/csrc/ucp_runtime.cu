@@ -66,6 +66,7 @@ struct ucp_ctx {
     double phi_theta = -1.0, phi_eps = -1.0;
     int64_t steps = 0, walk_targets = 0, walk_launches = 0;
     unsigned long long launch_base = 0;
+    unsigned int sort_epoch = 16;     // tags of the sort's published words (8 per build)
 
     bool prof = false;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
@@ -155,7 +156,8 @@ int build(ucp_ctx* c)
     launch_bbox(c->st[k][0], c->st[k][1], c->st[k][2], n, c->bbox_part, c->bbox_nblk, c->cube,
                 c->s);
     launch_keys(c->st[k][0], c->st[k][1], c->st[k][2], n, c->cube, c->key[0], c->val[0], c->s);
-    launch_sort(c->key, c->val, n, c->sort, c->id[k], c->s);
+    launch_sort(c->key, c->val, n, c->sort, c->id[k], c->sort_epoch, c->s);
+    c->sort_epoch += 8;
     const double* src[6];
     double* dst[6];
     for (int a = 0; a < 6; ++a) {
@@ -224,6 +226,17 @@ int force(ucp_ctx* c, double theta, double eps, int electrons_only, bool want_ph
         c->phi_eps = eps;
     }
     return check_launch(c, "tree walk");
+}
+
+// A bounded device-side wait that gave up leaves a flag; calls that synchronise
+// report it (the flag stays raised until the next ucp_set_state).
+int device_error(ucp_ctx* c)
+{
+    int e = 0;
+    if (cudaMemcpy(&e, c->sort.err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return fail(c, UCP_ECUDA, "reading the device error flag failed");
+    if (e) return fail(c, UCP_ETIMEOUT, "a device-side wait of the key sort gave up");
+    return UCP_OK;
 }
 
 int valid_walk_args(ucp_ctx* c, double theta, double eps)
@@ -309,13 +322,16 @@ int ucp_create(ucp_ctx** out, const ucp_params* p)
     if ((rc = dalloc(c, &c->ax, n)) || (rc = dalloc(c, &c->ay, n)) || (rc = dalloc(c, &c->az, n)) ||
         (rc = dalloc(c, &c->phi, n)))
         return bail(rc);
-    size_t sw = sort_scratch_words(c->n);
-    c->sort.nblocks = (int)(sw / 256);
-    if ((rc = dalloc(c, &c->sort.hist, sw)) ||
-        (rc = dalloc(c, &c->sort.hist_part, scan_partials_words((int)sw))))
+    if ((rc = dalloc(c, &c->sort.ghist, 8 * 256 + 8)) || (rc = dalloc(c, &c->sort.goff, 8 * 256)) ||
+        (rc = dalloc(c, &c->sort.status, sort_status_words(c->n))) ||
+        (rc = dalloc(c, &c->sort.err, 1)) ||
+        (rc = dalloc(c, &c->sort.test_keys, sort_test_words())) ||
+        (rc = dalloc(c, &c->sort.test_vals, sort_test_words())))
         return bail(rc);
+    if (cudaMemsetAsync(c->sort.status, 0, 8 * sort_status_words(c->n), c->s) != cudaSuccess ||
+        cudaMemsetAsync(c->sort.err, 0, sizeof(int), c->s) != cudaSuccess)
+        return bail(UCP_ECUDA);
     size_t spw = scan_partials_words(c->n);
-    if (spw < scan_partials_words((int)sw)) spw = scan_partials_words((int)sw);
     if ((rc = dalloc(c, &c->scan_part, spw))) return bail(rc);
     if ((rc = dalloc(c, &c->pos_cnt, n)) || (rc = dalloc(c, &c->pos_off, n))) return bail(rc);
     c->t.cap = (int)cap;
@@ -422,6 +438,7 @@ int ucp_set_state(ucp_ctx* c, const double* pos, const double* vel, const int8_t
     launch_deinterleave(dpos, c->n, c->st[k][0], c->st[k][1], c->st[k][2], c->s);
     launch_deinterleave(dvel, c->n, c->st[k][3], c->st[k][4], c->st[k][5], c->s);
     launch_iota(c->id[k], c->n, c->s);
+    CK(cudaMemsetAsync(c->sort.err, 0, sizeof(int), c->s));
     c->have_state = true;
     c->tree_valid = false;
     c->acc_valid = false;
@@ -451,7 +468,10 @@ int ucp_get_state(ucp_ctx* c, double* pos, double* vel, int on_device)
     }
     int rc = check_launch(c, "get_state");
     if (rc) return rc;
-    if (!on_device) CK(cudaStreamSynchronize(c->s));
+    if (!on_device) {
+        CK(cudaStreamSynchronize(c->s));
+        if ((rc = device_error(c))) return rc;
+    }
     return UCP_OK;
 }
 
@@ -486,7 +506,10 @@ int ucp_tree_force(ucp_ctx* c, double theta, double eps, double* acc, double* ph
             CK(cudaMemcpyAsync(phi, dst, n * sizeof(double), cudaMemcpyDeviceToHost, c->s));
     }
     if ((rc = check_launch(c, "tree_force"))) return rc;
-    if (!on_device) CK(cudaStreamSynchronize(c->s));
+    if (!on_device) {
+        CK(cudaStreamSynchronize(c->s));
+        if ((rc = device_error(c))) return rc;
+    }
     return UCP_OK;
 }
 
@@ -555,6 +578,7 @@ int ucp_energy(ucp_ctx* c, double theta, double eps, double out[6])
     CK(cudaMemcpyAsync(r, c->en_out, sizeof(r), cudaMemcpyDeviceToHost, c->s));
     CK(cudaStreamSynchronize(c->s));
     if ((rc = check_launch(c, "energy"))) return rc;
+    if ((rc = device_error(c))) return rc;
     out[0] = r[0];
     out[1] = r[1];
     out[2] = r[2];
@@ -575,6 +599,7 @@ int ucp_stats(ucp_ctx* c, int64_t out[8], int reset)
         CK(cudaMemcpyAsync(&md, c->t.maxdepth, sizeof(int), cudaMemcpyDeviceToHost, c->s));
     }
     CK(cudaStreamSynchronize(c->s));
+    int derr = device_error(c);
     out[0] = (int64_t)s2[0];
     out[1] = (int64_t)s2[1];
     out[2] = c->walk_targets;
@@ -591,7 +616,7 @@ int ucp_stats(ucp_ctx* c, int64_t out[8], int reset)
         c->walk_targets = 0;
         c->walk_launches = 0;
     }
-    return UCP_OK;
+    return derr;
 }
 
 int ucp_get_cube(ucp_ctx* c, double out[4])
@@ -702,6 +727,20 @@ int ucp_get_counts(ucp_ctx* c, int32_t* p2p, int32_t* m2p, int on_device)
     if (rc) return rc;
     if (!on_device) CK(cudaStreamSynchronize(c->s));
     return UCP_OK;
+}
+
+int ucp_selftest_wait_timeout(ucp_ctx* c)
+{
+    if (!c) return UCP_EINVAL;
+    CK(cudaStreamSynchronize(c->s));
+    CK(cudaMemsetAsync(c->sort.err, 0, sizeof(int), c->s));
+    if (sort_selftest_timeout(c->sort, c->s)) return fail(c, UCP_ECUDA, "self-test launch failed");
+    int e = 0;
+    CK(cudaMemcpyAsync(&e, c->sort.err, sizeof(int), cudaMemcpyDeviceToHost, c->s));
+    CK(cudaStreamSynchronize(c->s));
+    CK(cudaMemsetAsync(c->sort.err, 0, sizeof(int), c->s));
+    CK(cudaStreamSynchronize(c->s));
+    return e ? UCP_ETIMEOUT : UCP_OK;
 }
 
 int ucp_profile(ucp_ctx* c, int enable)

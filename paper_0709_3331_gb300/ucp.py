@@ -23,7 +23,7 @@ UCP_ION, UCP_ELECTRON = 0, 1
 EXPORTS = ("ucp_create", "ucp_destroy", "ucp_set_state", "ucp_get_state", "ucp_tree_build",
            "ucp_tree_force", "ucp_step", "ucp_energy", "ucp_stats", "ucp_get_cube",
            "ucp_get_sorted", "ucp_get_tree", "ucp_get_counts", "ucp_profile", "ucp_profile_read",
-           "ucp_strerror", "ucp_last_error")
+           "ucp_strerror", "ucp_last_error", "ucp_selftest_wait_timeout")
 
 
 class UcpError(RuntimeError):
@@ -64,6 +64,8 @@ def lib():
         L.ucp_get_counts.argtypes = [vp, vp, vp, i32]
         L.ucp_profile.argtypes = [vp, i32]
         L.ucp_profile_read.argtypes = [vp, C.POINTER(dbl), C.POINTER(i64)]
+        L.ucp_selftest_wait_timeout.argtypes = [vp]
+        L.ucp_selftest_wait_timeout.restype = C.c_int
         L.ucp_strerror.argtypes = [i32]
         L.ucp_strerror.restype = C.c_char_p
         L.ucp_last_error.argtypes = [vp]
@@ -224,6 +226,11 @@ class Context:
         self._check(lib().ucp_get_counts(self._h, p2p.ctypes.data, m2p.ctypes.data, 0),
                     "ucp_get_counts")
         return p2p, m2p
+
+    def selftest_wait_timeout(self):
+        """Run the bounded-wait self-test; returns the status code (UCP_ETIMEOUT
+        means the wait gave up and reported it as it should)."""
+        return int(lib().ucp_selftest_wait_timeout(self._h))
 
     def profile(self, enable=True):
         self._check(lib().ucp_profile(self._h, int(bool(enable))), "ucp_profile")

@@ -317,3 +317,18 @@ def test_device_pointers(U, orc):
         a_host, p_host = ctx.tree_force(0.5, 0.01)
     assert np.array_equal(acc.cpu().numpy(), a_host)
     assert np.array_equal(phi.cpu().numpy(), p_host)
+
+
+def test_bounded_wait_reports_timeout(U, orc):
+    """A sort pass whose predecessor never publishes gives up after its bounded
+    wait, raises the error flag (read by the host as UCP_ETIMEOUT) and leaves
+    the context usable."""
+    c = gaussian_cloud(4096, 1.0, 41)
+    with _ctx(U, c, 16, U.UCP_FP32C) as ctx:
+        assert ctx.selftest_wait_timeout() == -5
+        acc, _ = ctx.tree_force(0.5, 0.01)
+        ctx.step(1e-3, 2, 2, 0.5, 0.01)
+        ctx.energy(0.5, 0.01)
+    T = orc.Tree(c.pos, c.species, c.q, leaf_cap=16)
+    E, _ = T.force(0.5, 0.01)
+    assert rel_rms(acc, E * (c.q[c.species] / c.m[c.species])[:, None]) <= FP32C_TOL
