@@ -102,26 +102,38 @@ __global__ void k_scan_apply(const int* __restrict__ in, int* __restrict__ out, 
 }
 
 // ---------------------------------------------------------------- cube
+// Ordered integer image of a finite double: comparing the images compares the
+// values, so min/max run on the integer ALU instead of the (scarce) FP64 pipe.
+__device__ __forceinline__ unsigned long long ord64(double v)
+{
+    unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+__device__ __forceinline__ double unord64(unsigned long long u)
+{
+    return __longlong_as_double((long long)((u >> 63) ? (u & 0x7fffffffffffffffull) : ~u));
+}
+
 __global__ void k_bbox_partial(const double* __restrict__ x, const double* __restrict__ y,
                                const double* __restrict__ z, int n, double* __restrict__ part)
 {
-    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    unsigned long long lo[3] = {~0ull, ~0ull, ~0ull}, hi[3] = {0ull, 0ull, 0ull};
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        double v[3] = {x[i], y[i], z[i]};
+        unsigned long long v[3] = {ord64(x[i]), ord64(y[i]), ord64(z[i])};
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            lo[a] = fmin(lo[a], v[a]);
-            hi[a] = fmax(hi[a], v[a]);
+            lo[a] = min(lo[a], v[a]);
+            hi[a] = max(hi[a], v[a]);
         }
     }
 #pragma unroll
     for (int a = 0; a < 3; ++a)
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
-            lo[a] = fmin(lo[a], __shfl_xor_sync(0xffffffffu, lo[a], o));
-            hi[a] = fmax(hi[a], __shfl_xor_sync(0xffffffffu, hi[a], o));
+            lo[a] = min(lo[a], __shfl_xor_sync(0xffffffffu, lo[a], o));
+            hi[a] = max(hi[a], __shfl_xor_sync(0xffffffffu, hi[a], o));
         }
-    __shared__ double s[32][6];
+    __shared__ unsigned long long s[32][6];
     int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     if (lane == 0)
         for (int a = 0; a < 3; ++a) {
@@ -132,10 +144,14 @@ __global__ void k_bbox_partial(const double* __restrict__ x, const double* __res
     if (threadIdx.x == 0) {
         for (int ww = 1; ww < (int)(blockDim.x >> 5); ++ww)
             for (int a = 0; a < 3; ++a) {
-                s[0][a] = fmin(s[0][a], s[ww][a]);
-                s[0][3 + a] = fmax(s[0][3 + a], s[ww][3 + a]);
+                s[0][a] = min(s[0][a], s[ww][a]);
+                s[0][3 + a] = max(s[0][3 + a], s[ww][3 + a]);
             }
-        for (int a = 0; a < 6; ++a) part[blockIdx.x * 6 + a] = s[0][a];
+        // an empty partial (more blocks than particles) keeps +/-inf
+        for (int a = 0; a < 3; ++a) {
+            part[blockIdx.x * 6 + a] = s[0][a] == ~0ull ? INFINITY : unord64(s[0][a]);
+            part[blockIdx.x * 6 + 3 + a] = s[0][3 + a] == 0ull ? -INFINITY : unord64(s[0][3 + a]);
+        }
     }
 }
 
@@ -710,25 +726,44 @@ __device__ __forceinline__ void finish_box_f32(const float* a, const double z[3]
     m64[MDELTA] = sqrtf(fmaf(e[0], e[0], fmaf(e[1], e[1], e[2] * e[2])));
 }
 
+// Sum of v over the aligned group of G lanes that holds this lane (xor butterfly,
+// the same order in every group).
+template <int G>
+__device__ __forceinline__ float group_sum(float v)
+{
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Leaves, 16 lanes per leaf: lane l sums particles begin + l, begin + l + 16, ...
 __global__ void __launch_bounds__(256)
 k_moments_leaves_f32(const double* __restrict__ x, const double* __restrict__ y,
                      const double* __restrict__ z, const int8_t* __restrict__ sp,
                      const double* __restrict__ qsp, const Cube* __restrict__ cube, Tree t,
                      float4* __restrict__ src32)
 {
+    constexpr int G = 16;
     const int nl = t.count[kMaxDepth + 1];
     const Cube cb = *cube;
     const float q0 = (float)qsp[0], q1 = (float)qsp[1];
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nl; i += gridDim.x * blockDim.x) {
-        const int node = t.leaf_list[i];
-        const int dl = t.depth_leaf[node];
-        const int4 inf = t.info[node];
+    const int sub = threadIdx.x & (G - 1);
+    const int groups = gridDim.x * (blockDim.x / G);
+    // the loop bound is uniform over each warp (two groups per warp step together)
+    const int first = blockIdx.x * (blockDim.x / G) + (threadIdx.x / G);
+    const int warp_first = first & ~1;
+    for (int base = warp_first; base < nl; base += groups) {
+        const int i = base + (first & 1);
+        const bool have = i < nl;
+        const int node = have ? t.leaf_list[i] : 0;
+        const int dl = have ? t.depth_leaf[node] : 0;
+        const int4 inf = have ? t.info[node] : make_int4(0, 0, 0, 0);
         double zc[3], side;
-        box_centre(cb, t.cell[node], dl & 255, zc, &side);
+        box_centre(cb, have ? t.cell[node] : 0ull, dl & 255, zc, &side);
         float a[14];
 #pragma unroll
         for (int k = 0; k < 14; ++k) a[k] = 0.f;
-        for (int j = inf.x; j < inf.y; ++j) {
+        for (int j = inf.x + sub; j < inf.y; j += G) {
             float qj = sp[j] ? q1 : q0;
             float aq = fabsf(qj);
             float yv[3] = {(float)(x[j] - zc[0]), (float)(y[j] - zc[1]), (float)(z[j] - zc[2])};
@@ -747,17 +782,23 @@ k_moments_leaves_f32(const double* __restrict__ x, const double* __restrict__ y,
             a[12] = fmaf(qy1, yv[2], a[12]);
             a[13] = fmaf(qj * yv[2], yv[2], a[13]);
         }
-        float m32[16];
-        double* m = t.mom + (size_t)node * kMom;
-        finish_box_f32(a, zc, m32, m);
-        float4* r32 = reinterpret_cast<float4*>(t.mom32 + (size_t)node * 16);
-        for (int k = 0; k < 4; ++k)
-            r32[k] = make_float4(m32[4 * k], m32[4 * k + 1], m32[4 * k + 2], m32[4 * k + 3]);
+#pragma unroll
+        for (int k = 0; k < 14; ++k) a[k] = group_sum<G>(a[k]);
+        if (have && sub == 0) {
+            float m32[16];
+            finish_box_f32(a, zc, m32, t.mom + (size_t)node * kMom);
+            float4* r32 = reinterpret_cast<float4*>(t.mom32 + (size_t)node * 16);
+            for (int k = 0; k < 4; ++k)
+                r32[k] = make_float4(m32[4 * k], m32[4 * k + 1], m32[4 * k + 2], m32[4 * k + 3]);
+        }
+        // the centre exactly as finish_box_f32 stores it
+        const float inv = a[0] > 0.f ? 1.f / a[0] : 0.f;
+        const double cx = zc[0] + (double)(a[2] * inv), cy = zc[1] + (double)(a[3] * inv),
+                     cz = zc[2] + (double)(a[4] * inv);
         // paired sources: src32[2p] = {nx_2p, nx_2p+1, ny_2p, ny_2p+1},
         // src32[2p+1] = {nz_2p, nz_2p+1, q_2p, q_2p+1}, n = c_leaf - x
-        const double cx = m[MC], cy = m[MC + 1], cz = m[MC + 2];
         float* f = reinterpret_cast<float*>(src32);
-        for (int j = inf.x; j < inf.y; ++j) {
+        for (int j = inf.x + sub; j < inf.y; j += G) {
             size_t b = (size_t)(j >> 1) * 8 + (j & 1);
             f[b] = (float)(cx - x[j]);
             f[b + 2] = (float)(cy - y[j]);
@@ -767,57 +808,65 @@ k_moments_leaves_f32(const double* __restrict__ x, const double* __restrict__ y,
     }
 }
 
+// Twigs, 8 lanes per twig: lane o shifts child slot o to the twig's centre,
+// the group sums the eight contributions.
 __global__ void __launch_bounds__(256)
 k_moments_twigs_f32(const Cube* __restrict__ cube, Tree t, int d_hi, int d_lo)
 {
+    constexpr int G = 8;
     const Cube cb = *cube;
+    const int o = threadIdx.x & (G - 1);
+    const int groups = gridDim.x * (blockDim.x / G);
+    const int first = blockIdx.x * (blockDim.x / G) + (threadIdx.x / G);
+    const int warp_first = first & ~3;
     // several depths in one launch only with a single block (barrier between depths)
     for (int d = d_hi; d >= d_lo; --d) {
-    const int nt = t.count[d];
-    const int* __restrict__ list = t.twig_list + t.twig_off[d];
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nt; i += gridDim.x * blockDim.x) {
-        const int p = list[i];
-        double zp[3], ps;
-        box_centre(cb, t.cell[p], d, zp, &ps);
-        const int4 c03 = *reinterpret_cast<const int4*>(t.child8 + (size_t)p * 8);
-        const int4 c47 = *reinterpret_cast<const int4*>(t.child8 + (size_t)p * 8 + 4);
-        const int chs[8] = {c03.x, c03.y, c03.z, c03.w, c47.x, c47.y, c47.z, c47.w};
-        float a[14];
+        const int nt = t.count[d];
+        const int* __restrict__ list = t.twig_list + t.twig_off[d];
+        for (int base = warp_first; base < nt; base += groups) {
+            const int i = base + (first & 3);
+            const bool have = i < nt;
+            const int p = have ? list[i] : 0;
+            double zp[3], ps;
+            box_centre(cb, have ? t.cell[p] : 0ull, d, zp, &ps);
+            const int ch = have ? t.child8[(size_t)p * 8 + o] : -1;
+            float a[14];
 #pragma unroll
-        for (int k = 0; k < 14; ++k) a[k] = 0.f;
-#pragma unroll 1
-        for (int o = 0; o < 8; ++o) {
-            const int ch = chs[o];
-            if (ch < 0) continue;
-            const double* cm = t.mom + (size_t)ch * kMom;
-            const float4* r32 = reinterpret_cast<const float4*>(t.mom32 + (size_t)ch * 16);
-            const float4 R1 = r32[1], R2 = r32[2], R3 = r32[3];
-            const float S0k = r32[0].w, Mk = R1.x;
-            const float dk[3] = {R1.y, R1.z, R1.w};
-            const float qk[6] = {R2.x, R2.y, R2.z, R2.w, R3.x, R3.y};
-            float e[3];
-            for (int k = 0; k < 3; ++k) e[k] = (float)(cm[MC + k] - zp[k]);
-            a[0] += S0k;
-            a[1] += Mk;
-            for (int k = 0; k < 3; ++k) {
-                a[2 + k] = fmaf(S0k, e[k], a[2 + k]);
-                a[5 + k] += fmaf(Mk, e[k], dk[k]);
+            for (int k = 0; k < 14; ++k) a[k] = 0.f;
+            if (ch >= 0) {
+                const double* cm = t.mom + (size_t)ch * kMom;
+                const float4* r32 = reinterpret_cast<const float4*>(t.mom32 + (size_t)ch * 16);
+                const float4 R0 = r32[0], R1 = r32[1], R2 = r32[2], R3 = r32[3];
+                const float S0k = R0.w, Mk = R1.x;
+                const float dk[3] = {R1.y, R1.z, R1.w};
+                const float qk[6] = {R2.x, R2.y, R2.z, R2.w, R3.x, R3.y};
+                float e[3];
+                for (int k = 0; k < 3; ++k) e[k] = (float)(cm[MC + k] - zp[k]);
+                a[0] = S0k;
+                a[1] = Mk;
+                for (int k = 0; k < 3; ++k) {
+                    a[2 + k] = S0k * e[k];
+                    a[5 + k] = fmaf(Mk, e[k], dk[k]);
+                }
+                float me0 = Mk * e[0], me1 = Mk * e[1], me2 = Mk * e[2];
+                a[8] = qk[0] + (2.f * dk[0] + me0) * e[0];
+                a[9] = qk[1] + dk[0] * e[1] + (dk[1] + me1) * e[0];
+                a[10] = qk[2] + dk[0] * e[2] + (dk[2] + me2) * e[0];
+                a[11] = qk[3] + (2.f * dk[1] + me1) * e[1];
+                a[12] = qk[4] + dk[1] * e[2] + (dk[2] + me2) * e[1];
+                a[13] = qk[5] + (2.f * dk[2] + me2) * e[2];
             }
-            float me0 = Mk * e[0], me1 = Mk * e[1], me2 = Mk * e[2];
-            a[8] += qk[0] + (2.f * dk[0] + me0) * e[0];
-            a[9] += qk[1] + dk[0] * e[1] + (dk[1] + me1) * e[0];
-            a[10] += qk[2] + dk[0] * e[2] + (dk[2] + me2) * e[0];
-            a[11] += qk[3] + (2.f * dk[1] + me1) * e[1];
-            a[12] += qk[4] + dk[1] * e[2] + (dk[2] + me2) * e[1];
-            a[13] += qk[5] + (2.f * dk[2] + me2) * e[2];
+#pragma unroll
+            for (int k = 0; k < 14; ++k) a[k] = group_sum<G>(a[k]);
+            if (have && o == 0) {
+                float m32[16];
+                finish_box_f32(a, zp, m32, t.mom + (size_t)p * kMom);
+                float4* w32 = reinterpret_cast<float4*>(t.mom32 + (size_t)p * 16);
+                for (int k = 0; k < 4; ++k)
+                    w32[k] = make_float4(m32[4 * k], m32[4 * k + 1], m32[4 * k + 2], m32[4 * k + 3]);
+            }
         }
-        float m32[16];
-        finish_box_f32(a, zp, m32, t.mom + (size_t)p * kMom);
-        float4* w32 = reinterpret_cast<float4*>(t.mom32 + (size_t)p * 16);
-        for (int k = 0; k < 4; ++k)
-            w32[k] = make_float4(m32[4 * k], m32[4 * k + 1], m32[4 * k + 2], m32[4 * k + 3]);
-    }
-    if (d > d_lo) __syncthreads();
+        if (d > d_lo) __syncthreads();
     }
 }
 
@@ -925,7 +974,7 @@ void launch_moments(const double* x, const double* y, const double* z, const int
                     const double* qsp, int n, const Cube* cube, Tree t, float4* src32,
                     int want_f32, cudaStream_t s)
 {
-    count_launch(1 + 10);
+    count_launch(1 + 12);
     int blocks = (n + 255) / 256;
     if (blocks > 4 * 152) blocks = 4 * 152;
     if (blocks < 1) blocks = 1;
@@ -933,20 +982,20 @@ void launch_moments(const double* x, const double* y, const double* z, const int
         k_moments_leaves_f32<<<blocks, 256, 0, s>>>(x, y, z, sp, qsp, cube, t, src32);
     else
         k_moments_leaves<<<blocks, 256, 0, s>>>(x, y, z, sp, qsp, cube, t, src32, 0);
-    // deep depths (usually empty) and the top depths (at most 8^4 twigs) each in
+    // deep depths (usually empty) and the top depths (at most 8^2 twigs) each in
     // one single-block launch; the middle depths one multi-block launch each
     auto twigs = [&](int d_hi, int d_lo, int b) {
         if (want_f32) k_moments_twigs_f32<<<b, 256, 0, s>>>(cube, t, d_hi, d_lo);
         else k_moments_twigs<<<b, 256, 0, s>>>(cube, t, d_hi, d_lo);
     };
     twigs(kMaxDepth - 1, 13, 1);
-    for (int d = 12; d >= 5; --d) {
+    for (int d = 12; d >= 3; --d) {
         int cap = t.twig_off[d + 1] - t.twig_off[d];
-        int b = (cap + 255) / 256;
-        if (b > 2 * 152) b = 2 * 152;
+        int b = (cap + 31) / 32;
+        if (b > 4 * 152) b = 4 * 152;
         twigs(d, d, b < 1 ? 1 : b);
     }
-    twigs(4, 0, 1);
+    twigs(2, 0, 1);
 }
 
 }  // namespace ucp
