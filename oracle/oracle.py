@@ -83,6 +83,7 @@ def lib():
             L.orc_energy.argtypes = [C.c_int64, _d, _d, _i8, _d, _d, C.c_double, C.c_double,
                                      C.c_int, C.c_int, _d, C.c_int]
             L.orc_has_openmp.restype = C.c_int
+            L.orc_set_potential.argtypes = [C.c_int, C.c_double]
             L.orc_cluster_multipole.argtypes = [C.c_int64, _d, _i8, _d, C.c_double, _d, C.c_int,
                                                 _d, _d]
             _lib = L
@@ -103,6 +104,21 @@ def _qm(v):
 
 def _ptr(a):
     return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+class kelbg:
+    """Context manager: direct electron-ion pairs use the Kelbg form (Sec. 2.1
+    Eq. 3) with a fixed lambda inside the block; Plummer Coulomb outside."""
+
+    def __init__(self, lam):
+        self.lam = float(lam)
+
+    def __enter__(self):
+        lib().orc_set_potential(1, self.lam)
+        return self
+
+    def __exit__(self, *exc):
+        lib().orc_set_potential(0, 1.0)
 
 
 def has_openmp() -> bool:

@@ -54,14 +54,48 @@
 #define ORC_KMAX ((uint32_t)1 << ORC_MAXDEPTH) /* 2^21 cells per axis */
 
 /* ------------------------------------------------------------------ */
-/* Sec. 2.1 Eq. 1-2 (R1): one softened pair; adds the field at xt due to a
- * charge qj at xj (field = force per unit target charge) and the potential. */
-static void pair_field(const double xt[3], const double xj[3], double qj,
+/* Interaction law of a direct pair.  g_kelbg = 0: Plummer-softened Coulomb for
+ * every pair (R1).  g_kelbg = 1: the Kelbg form of Sec. 2.1 Eq. 3 for an
+ * electron-ion pair, V = q_i q_j (1 - exp(-r/lambda)) / r with lambda fixed
+ * (Sec. 2.1 fixes lambda_ei to one value instead of the thermal wavelength),
+ * and bare (softened) Coulomb for like pairs; multipoles stay Coulomb, since the
+ * exponential term is negligible in the far field (Sec. 2.1). */
+static int g_kelbg = 0;
+static double g_lambda = 1.0;
+
+void orc_set_potential(int kelbg, double lambda)
+{
+    g_kelbg = kelbg;
+    g_lambda = lambda;
+}
+
+/* Adds the field at xt due to a charge qj at xj (field = force per unit target
+ * charge) and the potential.  unlike = the two particles are of different
+ * species. */
+static void pair_field(const double xt[3], const double xj[3], double qj, int unlike,
                        double eps2, double E[3], double* phi)
 {
     double dx = xt[0] - xj[0];
     double dy = xt[1] - xj[1];
     double dz = xt[2] - xj[2];
+    if (g_kelbg && unlike) {
+        /* V/q_t = qj (1 - e)/r, e = exp(-r/lambda);
+         * E = -grad = qj r_vec [(1 - e)/r^3 - e/(lambda r^2)] */
+        double r = sqrt(dx * dx + dy * dy + dz * dz);
+        if (r == 0.0) { /* limit r -> 0: potential qj/lambda, no force */
+            *phi += qj / g_lambda;
+            return;
+        }
+        double u = r / g_lambda;
+        double e = exp(-u);
+        double one_minus_e = -expm1(-u);
+        double f = (one_minus_e / (r * r * r)) - e / (g_lambda * r * r);
+        E[0] += qj * dx * f;
+        E[1] += qj * dy * f;
+        E[2] += qj * dz * f;
+        *phi += qj * one_minus_e / r;
+        return;
+    }
     double r2 = dx * dx + dy * dy + dz * dz + eps2;
     double rinv = 1.0 / sqrt(r2);
     double rinv3 = rinv * rinv * rinv;
@@ -89,7 +123,8 @@ void orc_direct(int64_t n, const double* pos, const int8_t* species,
         double E[3] = {0.0, 0.0, 0.0}, phi = 0.0;
         for (int64_t j = 0; j < n; ++j) {
             if (j == t) continue;
-            pair_field(&pos[3 * t], &pos[3 * j], q[species[j]], eps2, E, &phi);
+            pair_field(&pos[3 * t], &pos[3 * j], q[species[j]], species[j] != species[t], eps2,
+                       E, &phi);
         }
         E_out[3 * a + 0] = E[0];
         E_out[3 * a + 1] = E[1];
@@ -108,7 +143,13 @@ double orc_direct_pe(int64_t n, const double* pos, const int8_t* species,
             double dx = pos[3 * i] - pos[3 * j];
             double dy = pos[3 * i + 1] - pos[3 * j + 1];
             double dz = pos[3 * i + 2] - pos[3 * j + 2];
-            pe += q[species[i]] * q[species[j]] / sqrt(dx * dx + dy * dy + dz * dz + eps2);
+            if (g_kelbg && species[i] != species[j]) {
+                double r = sqrt(dx * dx + dy * dy + dz * dz);
+                pe += q[species[i]] * q[species[j]] *
+                      (r > 0.0 ? -expm1(-r / g_lambda) / r : 1.0 / g_lambda);
+            } else {
+                pe += q[species[i]] * q[species[j]] / sqrt(dx * dx + dy * dy + dz * dz + eps2);
+            }
         }
     return pe;
 }
@@ -463,7 +504,8 @@ static void walk(const walk_args* W, int64_t nd, int64_t t, const double xt[3],
         for (int64_t sl = T->begin[nd]; sl < T->end[nd]; ++sl) {
             int64_t j = T->slot[sl];
             if (j == t) continue;
-            pair_field(xt, &W->pos[3 * j], W->q[W->species[j]], W->eps2, E, phi);
+            pair_field(xt, &W->pos[3 * j], W->q[W->species[j]], W->species[j] != W->species[t],
+                       W->eps2, E, phi);
             (*np2p)++;
         }
         return;

@@ -736,34 +736,27 @@ __device__ __forceinline__ float group_sum(float v)
     return v;
 }
 
-// Leaves, 16 lanes per leaf: lane l sums particles begin + l, begin + l + 16, ...
+// Leaves, one thread per leaf (full lanes for the FP64 offsets).
 __global__ void __launch_bounds__(256)
 k_moments_leaves_f32(const double* __restrict__ x, const double* __restrict__ y,
                      const double* __restrict__ z, const int8_t* __restrict__ sp,
                      const double* __restrict__ qsp, const Cube* __restrict__ cube, Tree t,
                      float4* __restrict__ src32)
 {
-    constexpr int G = 16;
     const int nl = t.count[kMaxDepth + 1];
     const Cube cb = *cube;
     const float q0 = (float)qsp[0], q1 = (float)qsp[1];
-    const int sub = threadIdx.x & (G - 1);
-    const int groups = gridDim.x * (blockDim.x / G);
-    // the loop bound is uniform over each warp (two groups per warp step together)
-    const int first = blockIdx.x * (blockDim.x / G) + (threadIdx.x / G);
-    const int warp_first = first & ~1;
-    for (int base = warp_first; base < nl; base += groups) {
-        const int i = base + (first & 1);
-        const bool have = i < nl;
-        const int node = have ? t.leaf_list[i] : 0;
-        const int dl = have ? t.depth_leaf[node] : 0;
-        const int4 inf = have ? t.info[node] : make_int4(0, 0, 0, 0);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nl; i += gridDim.x * blockDim.x) {
+        const int node = t.leaf_list[i];
+        const int dl = t.depth_leaf[node];
+        const int4 inf = t.info[node];
         double zc[3], side;
-        box_centre(cb, have ? t.cell[node] : 0ull, dl & 255, zc, &side);
+        box_centre(cb, t.cell[node], dl & 255, zc, &side);
         float a[14];
 #pragma unroll
         for (int k = 0; k < 14; ++k) a[k] = 0.f;
-        for (int j = inf.x + sub; j < inf.y; j += G) {
+#pragma unroll 4
+        for (int j = inf.x; j < inf.y; ++j) {
             float qj = sp[j] ? q1 : q0;
             float aq = fabsf(qj);
             float yv[3] = {(float)(x[j] - zc[0]), (float)(y[j] - zc[1]), (float)(z[j] - zc[2])};
@@ -782,23 +775,17 @@ k_moments_leaves_f32(const double* __restrict__ x, const double* __restrict__ y,
             a[12] = fmaf(qy1, yv[2], a[12]);
             a[13] = fmaf(qj * yv[2], yv[2], a[13]);
         }
-#pragma unroll
-        for (int k = 0; k < 14; ++k) a[k] = group_sum<G>(a[k]);
-        if (have && sub == 0) {
-            float m32[16];
-            finish_box_f32(a, zc, m32, t.mom + (size_t)node * kMom);
-            float4* r32 = reinterpret_cast<float4*>(t.mom32 + (size_t)node * 16);
-            for (int k = 0; k < 4; ++k)
-                r32[k] = make_float4(m32[4 * k], m32[4 * k + 1], m32[4 * k + 2], m32[4 * k + 3]);
-        }
-        // the centre exactly as finish_box_f32 stores it
-        const float inv = a[0] > 0.f ? 1.f / a[0] : 0.f;
-        const double cx = zc[0] + (double)(a[2] * inv), cy = zc[1] + (double)(a[3] * inv),
-                     cz = zc[2] + (double)(a[4] * inv);
+        float m32[16];
+        double* m = t.mom + (size_t)node * kMom;
+        finish_box_f32(a, zc, m32, m);
+        float4* r32 = reinterpret_cast<float4*>(t.mom32 + (size_t)node * 16);
+        for (int k = 0; k < 4; ++k)
+            r32[k] = make_float4(m32[4 * k], m32[4 * k + 1], m32[4 * k + 2], m32[4 * k + 3]);
         // paired sources: src32[2p] = {nx_2p, nx_2p+1, ny_2p, ny_2p+1},
         // src32[2p+1] = {nz_2p, nz_2p+1, q_2p, q_2p+1}, n = c_leaf - x
+        const double cx = m[MC], cy = m[MC + 1], cz = m[MC + 2];
         float* f = reinterpret_cast<float*>(src32);
-        for (int j = inf.x + sub; j < inf.y; j += G) {
+        for (int j = inf.x; j < inf.y; ++j) {
             size_t b = (size_t)(j >> 1) * 8 + (j & 1);
             f[b] = (float)(cx - x[j]);
             f[b + 2] = (float)(cy - y[j]);

@@ -75,3 +75,51 @@ def batched_sizes(n_clouds: int = 64, seed: int = 4):
     u = rng.uniform(math.log(4096), math.log(65536), size=n_clouds)
     ns = [int(2 * round(math.exp(v) / 2)) for v in u]
     return ns, [(nc / 2048.0) ** (1.0 / 3.0) for nc in ns]
+
+
+# Physical constants (CODATA 2018) for the Sec. 5 set-up.
+_E = 1.602176634e-19
+_EPS0 = 8.8541878128e-12
+_KB = 1.380649e-23
+_ME = 9.1093837015e-31
+_AMU = 1.66053906660e-27
+
+
+def sec5_units(density_per_cm3, lambda_ei_angstrom, t_e_kelvin, t_i_kelvin, ion_mass_amu,
+               dt_fs):
+    """Reduced units for a physical set-up: length = Wigner-Seitz radius a of the
+    density, energy = e^2 / (4 pi eps0 a), mass = electron mass, time =
+    sqrt(m_e a^3 4 pi eps0 / e^2).  Returns lambda, temperatures (k_B T in energy
+    units), ion mass and time step in those units, and the units themselves."""
+    n = density_per_cm3 * 1e6
+    a = (3.0 / (4.0 * math.pi * n)) ** (1.0 / 3.0)
+    energy = _E * _E / (4.0 * math.pi * _EPS0 * a)
+    tau = math.sqrt(_ME * a ** 3 * 4.0 * math.pi * _EPS0 / (_E * _E))
+    return {"length_m": a, "energy_j": energy, "time_s": tau,
+            "lambda": lambda_ei_angstrom * 1e-10 / a,
+            "t_e": _KB * t_e_kelvin / energy, "t_i": _KB * t_i_kelvin / energy,
+            "m_i": ion_mass_amu * _AMU / _ME, "dt": dt_fs * 1e-15 / tau}
+
+
+def uniform_sphere(n, radius, seed, t_e, t_i, m_i, m_e=1.0):
+    """N/2 ions then N/2 electrons uniformly in a sphere (the Sec. 5 cloud shape),
+    Maxwellian velocities with each species' mean removed."""
+    if n < 0 or n % 2:
+        raise ValueError("n must be a non-negative even number")
+    h = n // 2
+    rng = np.random.default_rng(seed)
+    pos = np.empty((n, 3))
+    for lo, hi in ((0, h), (h, n)):
+        d = rng.normal(size=(hi - lo, 3))
+        d /= np.linalg.norm(d, axis=1)[:, None]
+        pos[lo:hi] = d * (radius * rng.uniform(size=(hi - lo, 1)) ** (1.0 / 3.0))
+    vel = np.empty((n, 3))
+    vel[:h] = rng.normal(0.0, math.sqrt(t_i / m_i), size=(h, 3))
+    vel[h:] = rng.normal(0.0, math.sqrt(t_e / m_e), size=(h, 3))
+    if h:
+        vel[:h] -= vel[:h].mean(axis=0)
+        vel[h:] -= vel[h:].mean(axis=0)
+    species = np.empty(n, dtype=np.int8)
+    species[:h] = ION
+    species[h:] = ELECTRON
+    return Cloud(pos, vel, species, np.array([1.0, -1.0]), np.array([m_i, m_e]))
