@@ -45,6 +45,12 @@ enum {
 };
 
 enum { UCP_FP64 = 0, UCP_FP32C = 1 };  /* arithmetic of the force walk */
+/* Direct-pair law: UCP_POT_PLUMMER = q_i q_j / sqrt(r^2 + eps^2) for every pair;
+ * UCP_POT_KELBG = the Kelbg form q_i q_j (1 - exp(-r/lambda_ei)) / r of Sec. 2.1
+ * Eq. 3 for electron-ion pairs (lambda_ei fixed, as Sec. 2.1 does), softened
+ * Coulomb for like pairs; multipoles of accepted boxes stay Coulomb in both
+ * (the exponential term is negligible in the far field, Sec. 2.1). */
+enum { UCP_POT_PLUMMER = 0, UCP_POT_KELBG = 1 };
 enum { UCP_ION = 0, UCP_ELECTRON = 1 }; /* species codes */
 
 typedef struct ucp_ctx ucp_ctx;
@@ -59,6 +65,9 @@ typedef struct {
     double q[2];        /* charge per species [ion, electron] */
     double m[2];        /* mass per species, > 0 */
     void* cuda_stream;  /* cudaStream_t the context works on (NULL = legacy) */
+    int32_t potential;  /* UCP_POT_PLUMMER (0) or UCP_POT_KELBG (needs q[0] != q[1]) */
+    int32_t reserved;   /* 0 */
+    double lambda_ei;   /* Kelbg length, > 0 (reduced units); ignored for Plummer */
 } ucp_params;
 
 /* Create a context for params->n particles and allocate all device memory

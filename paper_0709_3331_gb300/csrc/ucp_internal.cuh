@@ -95,6 +95,8 @@ struct WalkArgs {
     const int* targets;     // key-order slots of the targets, or NULL = all
     int ntargets;
     double eps2;
+    int kelbg;              // electron-ion pairs use the Kelbg form (Sec. 2.1 Eq. 3)
+    double lambda;          // its fixed lambda_ei
     double* ax; double* ay; double* az; double* phi;  // key order; phi may be NULL
     int* cnt_p2p; int* cnt_m2p;                        // key order
     int* work;              // dynamic work counter (zeroed before launch)

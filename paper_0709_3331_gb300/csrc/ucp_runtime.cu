@@ -20,6 +20,8 @@ std::atomic<unsigned long long> ucp::g_launches{0};
 
 struct ucp_ctx {
     int n = 0, leaf_cap = 1, precision = UCP_FP64;
+    int potential = UCP_POT_PLUMMER;
+    double lambda_ei = 1.0;
     double q[2] = {1, -1}, m[2] = {1, 1};
     cudaStream_t s = nullptr;
     int nsm = 152;
@@ -201,6 +203,8 @@ int force(ucp_ctx* c, double theta, double eps, int electrons_only, bool want_ph
         a.ntargets = c->n;
     }
     a.eps2 = eps * eps;
+    a.kelbg = c->potential == UCP_POT_KELBG;
+    a.lambda = c->lambda_ei;
     a.ax = c->ax;
     a.ay = c->ay;
     a.az = c->az;
@@ -289,6 +293,10 @@ int ucp_create(ucp_ctx** out, const ucp_params* p)
     for (int s = 0; s < 2; ++s)
         if (!(p->m[s] > 0.0) || !std::isfinite(p->m[s]) || !std::isfinite(p->q[s]))
             return UCP_EINVAL;
+    if (p->potential != UCP_POT_PLUMMER && p->potential != UCP_POT_KELBG) return UCP_EINVAL;
+    if (p->potential == UCP_POT_KELBG &&
+        (!(p->lambda_ei > 0.0) || !std::isfinite(p->lambda_ei) || p->q[0] == p->q[1]))
+        return UCP_EINVAL;
     int64_t cap = box_capacity(p->n, p->leaf_cap);
     if (cap > 0x7ffffff0LL) return UCP_EINVAL;
 
@@ -297,6 +305,8 @@ int ucp_create(ucp_ctx** out, const ucp_params* p)
     c->n = (int)p->n;
     c->leaf_cap = p->leaf_cap;
     c->precision = p->precision;
+    c->potential = p->potential;
+    c->lambda_ei = p->potential == UCP_POT_KELBG ? p->lambda_ei : 1.0;
     for (int s = 0; s < 2; ++s) {
         c->q[s] = p->q[s];
         c->m[s] = p->m[s];

@@ -107,6 +107,7 @@ __device__ __forceinline__ void m2p<float>(float rx, float ry, float rz, float r
     ez = fmaf(mg3, fmaf(s3, QRz, Dz), fmaf(aa, rz, ez));
 }
 
+template <bool kKelbg>
 __global__ void __launch_bounds__(kWalkThreads)
 k_walk_fp64(WalkArgs a)
 {
@@ -129,6 +130,7 @@ k_walk_fp64(WalkArgs a)
         const bool valid = ti < a.ntargets;
         const int t = valid ? (a.targets ? a.targets[ti] : ti) : -1;
         const double xt = valid ? X[t] : 0.0, yt = valid ? Y[t] : 0.0, zt = valid ? Z[t] : 0.0;
+        const int8_t st = valid ? SP[t] : 0;
         double ex = 0.0, ey = 0.0, ez = 0.0, ph = 0.0;
         int np = 0, nm = 0;
         int skip = valid ? 0 : 0x7fffffff;
@@ -144,6 +146,24 @@ k_walk_fp64(WalkArgs a)
                         if (j == t) continue;
                         double qj = SP[j] ? q1 : q0;
                         double dx = xt - X[j], dy = yt - Y[j], dz = zt - Z[j];
+                        if (kKelbg && SP[j] != st) {
+                            // Sec. 2.1 Eq. 3: qj (1 - e)/r, e = exp(-r/lambda);
+                            // E = qj r_vec [(1 - e)/r^3 - e/(lambda r^2)]
+                            double r = sqrt(dx * dx + dy * dy + dz * dz);
+                            ++np;
+                            if (r == 0.0) {
+                                ph += qj / a.lambda;
+                                continue;
+                            }
+                            double u = r / a.lambda;
+                            double e = exp(-u), ome = -expm1(-u);
+                            double f = ome / (r * r * r) - e / (a.lambda * r * r);
+                            ex += qj * dx * f;
+                            ey += qj * dy * f;
+                            ez += qj * dz * f;
+                            ph += qj * ome / r;
+                            continue;
+                        }
                         double r2 = dx * dx + dy * dy + dz * dz + a.eps2;
                         double ri = rsqrt(r2);
                         double qr3 = qj * ri * ri * ri;
@@ -221,6 +241,28 @@ k_walk_fp64(WalkArgs a)
 }
 
 // ------------------------------------------------------------------ FP32C
+// Kelbg pair factors in FP32 for u = r/lambda: p = (1 - e^-u)/u and
+// g = (1 - (1 + u) e^-u)/u^3, by their Taylor series below u = 1/2 (no
+// cancellation) and directly above.
+__device__ __forceinline__ void kelbg_pg(float u, float& p, float& g)
+{
+    if (u < 0.5f) {
+        p = fmaf(u, fmaf(u, fmaf(u, fmaf(u, fmaf(u, fmaf(u, 1.f / 5040.f, -1.f / 720.f),
+                                                    1.f / 120.f), -1.f / 24.f), 1.f / 6.f),
+                          -0.5f), 1.f);
+        float poly = fmaf(u, fmaf(u, fmaf(u, fmaf(u, fmaf(u, 1.f / 5760.f, -1.f / 840.f),
+                                                  1.f / 144.f), -1.f / 30.f), 0.125f),
+                          -1.f / 3.f);
+        g = 0.5f / u + poly;
+    } else {
+        float e = __expf(-u);
+        float iu = 1.f / u;
+        p = (1.f - e) * iu;
+        g = (1.f - (1.f + u) * e) * iu * iu * iu;
+    }
+}
+
+template <bool kKelbg>
 __global__ void __launch_bounds__(kWalkThreads, 7)
 k_walk_fp32c(WalkArgs a)
 {
@@ -245,6 +287,9 @@ k_walk_fp32c(WalkArgs a)
             xh = (float)X; yh = (float)Y; zh = (float)Z;
             xl = (float)(X - (double)xh); yl = (float)(Y - (double)yh); zl = (float)(Z - (double)zh);
         }
+        const float qt = valid ? (a.sp[t] ? (float)q1 : (float)q0) : 0.f;
+        const float inv_lambda = (float)(1.0 / a.lambda);
+        const float inv_lambda3 = inv_lambda * inv_lambda * inv_lambda;
         // compensated totals (sum, correction) and the current multipole batch
         float sx = 0.f, sy = 0.f, sz = 0.f, sp = 0.f, cx = 0.f, cy = 0.f, cz = 0.f, cp = 0.f;
         float bx = 0.f, by = 0.f, bz = 0.f, bp = 0.f;
@@ -271,6 +316,50 @@ k_walk_fp32c(WalkArgs a)
                     float ry = (yh - A.y) + (yl - B.y);
                     float rz = (zh - A.z) + (zl - B.z);
                     int jb = __float_as_int(C.x), je = __float_as_int(C.y);
+                    if (kKelbg) {
+                        // one source at a time: unlike charges (electron-ion) take the
+                        // Kelbg form, like charges the softened Coulomb law
+                        float px = 0.f, py = 0.f, pz = 0.f, pp = 0.f;
+                        for (int j = jb; j < je; ++j) {
+                            if (j == t) continue;
+                            const float4 P = __ldg(S + (j & ~1)), Q = __ldg(S + (j & ~1) + 1);
+                            const bool odd = j & 1;
+                            float dx = rx + (odd ? P.y : P.x);
+                            float dy = ry + (odd ? P.w : P.z);
+                            float dz = rz + (odd ? Q.y : Q.x);
+                            float qj = odd ? Q.w : Q.z;
+                            if (qj != qt) {
+                                float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                                if (r2 == 0.f) {
+                                    pp = fmaf(qj, inv_lambda, pp);
+                                    continue;
+                                }
+                                float r = sqrtf(r2);
+                                float pf, gf;
+                                kelbg_pg(r * inv_lambda, pf, gf);
+                                float fq = qj * gf * inv_lambda3;
+                                px = fmaf(fq, dx, px);
+                                py = fmaf(fq, dy, py);
+                                pz = fmaf(fq, dz, pz);
+                                pp = fmaf(qj * inv_lambda, pf, pp);
+                            } else {
+                                float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
+                                float ri = rsqrtf(r2);
+                                float qi = qj * ri;
+                                float qr3 = qi * ri * ri;
+                                px = fmaf(qr3, dx, px);
+                                py = fmaf(qr3, dy, py);
+                                pz = fmaf(qr3, dz, pz);
+                                pp += qi;
+                            }
+                        }
+                        np += (je - jb) - ((t >= jb && t < je) ? 1 : 0);
+                        two_sum_acc(sx, cx, px);
+                        two_sum_acc(sy, cy, py);
+                        two_sum_acc(sz, cz, pz);
+                        two_sum_acc(sp, cp, pp);
+                        continue;
+                    }
                     // sources in pairs {x_2p, x_2p+1, y.., y..}, {z.., z.., q.., q..} as
                     // offsets c_leaf - x_j; a pair member outside [jb, je) or equal to
                     // the target gets a zero inverse distance
@@ -436,14 +525,16 @@ void launch_walk_fp64(const WalkArgs& a, int nsm, cudaStream_t s)
 {
     count_launch(1);
     cudaMemsetAsync(a.work, 0, sizeof(int), s);
-    k_walk_fp64<<<walk_blocks(a.ntargets, nsm, 8), kWalkThreads, 0, s>>>(a);
+    if (a.kelbg) k_walk_fp64<true><<<walk_blocks(a.ntargets, nsm, 8), kWalkThreads, 0, s>>>(a);
+    else k_walk_fp64<false><<<walk_blocks(a.ntargets, nsm, 8), kWalkThreads, 0, s>>>(a);
 }
 
 void launch_walk_fp32c(const WalkArgs& a, int nsm, cudaStream_t s)
 {
     count_launch(1);
     cudaMemsetAsync(a.work, 0, sizeof(int), s);
-    k_walk_fp32c<<<walk_blocks(a.ntargets, nsm, 12), kWalkThreads, 0, s>>>(a);
+    if (a.kelbg) k_walk_fp32c<true><<<walk_blocks(a.ntargets, nsm, 12), kWalkThreads, 0, s>>>(a);
+    else k_walk_fp32c<false><<<walk_blocks(a.ntargets, nsm, 12), kWalkThreads, 0, s>>>(a);
 }
 
 }  // namespace ucp

@@ -19,6 +19,7 @@ UCP_OK, UCP_EINVAL, UCP_ENOMEM, UCP_ECUDA, UCP_ENONFINITE, UCP_ETIMEOUT, UCP_EST
     0, -1, -2, -3, -4, -5, -6)
 UCP_FP64, UCP_FP32C = 0, 1
 UCP_ION, UCP_ELECTRON = 0, 1
+UCP_POT_PLUMMER, UCP_POT_KELBG = 0, 1
 
 EXPORTS = ("ucp_create", "ucp_destroy", "ucp_set_state", "ucp_get_state", "ucp_tree_build",
            "ucp_tree_force", "ucp_step", "ucp_energy", "ucp_stats", "ucp_get_cube",
@@ -34,7 +35,8 @@ class UcpError(RuntimeError):
 
 class ucp_params(C.Structure):
     _fields_ = [("n", C.c_int64), ("leaf_cap", C.c_int32), ("precision", C.c_int32),
-                ("q", C.c_double * 2), ("m", C.c_double * 2), ("cuda_stream", C.c_void_p)]
+                ("q", C.c_double * 2), ("m", C.c_double * 2), ("cuda_stream", C.c_void_p),
+                ("potential", C.c_int32), ("reserved", C.c_int32), ("lambda_ei", C.c_double)]
 
 
 _lib = None
@@ -103,7 +105,7 @@ class Context:
     """One particle set on the current CUDA device (``ucp_create`` .. ``ucp_destroy``)."""
 
     def __init__(self, n, q=(1.0, -1.0), m=(1000.0, 1.0), leaf_cap=16, precision=UCP_FP64,
-                 stream=None):
+                 stream=None, kelbg_lambda=None):
         L = lib()
         p = ucp_params()
         p.n = int(n)
@@ -119,6 +121,9 @@ class Context:
             except ImportError:
                 stream = None
         p.cuda_stream = stream
+        if kelbg_lambda is not None:
+            p.potential = UCP_POT_KELBG
+            p.lambda_ei = float(kelbg_lambda)
         self.n = int(n)
         self._h = C.c_void_p()
         rc = L.ucp_create(C.byref(self._h), C.byref(p))

@@ -332,3 +332,66 @@ def test_bounded_wait_reports_timeout(U, orc):
     T = orc.Tree(c.pos, c.species, c.q, leaf_cap=16)
     E, _ = T.force(0.5, 0.01)
     assert rel_rms(acc, E * (c.q[c.species] / c.m[c.species])[:, None]) <= FP32C_TOL
+
+
+# ----------------------------------------------------------------- Kelbg (Sec. 2.1 Eq. 3)
+@pytest.mark.parametrize("prec,tol", [(0, FP64_TOL), (1, FP32C_TOL)])
+@pytest.mark.parametrize("lam", [0.02, 0.3])
+def test_kelbg_force(U, orc, prec, tol, lam):
+    c = gaussian_cloud(2048, 1.0, 1)
+    with orc.kelbg(lam):
+        T = orc.Tree(c.pos, c.species, c.q, leaf_cap=16)
+        E, phi = T.force(0.5, 0.01, nthreads=4)
+    a_ref = E * (c.q[c.species] / c.m[c.species])[:, None]
+    with U.Context(c.n, c.q, c.m, leaf_cap=16, precision=prec, kelbg_lambda=lam) as ctx:
+        ctx.set_state(c.pos, c.vel, c.species)
+        acc, ph = ctx.tree_force(0.5, 0.01)
+    assert rel_rms(acc, a_ref) <= tol
+    assert rel_rms(ph, phi) <= tol
+
+
+def test_kelbg_coincident_pair(U, orc):
+    pos = np.array([[0.1, 0.2, 0.3], [0.1, 0.2, 0.3], [1.0, 0.0, 0.0], [0.0, 1.5, 0.0]])
+    sp = np.array([0, 1, 0, 1], dtype=np.int8)
+    vel = np.zeros((4, 3))
+    q, m = np.array([1.0, -1.0]), np.array([1000.0, 1.0])
+    with orc.kelbg(0.2):
+        E, phi = orc.direct(pos, sp, q, 0.01)
+    for prec, tol in ((0, 1e-12), (1, 1e-5)):
+        with U.Context(4, q, m, leaf_cap=1, precision=prec, kelbg_lambda=0.2) as ctx:
+            ctx.set_state(pos, vel, sp)
+            acc, ph = ctx.tree_force(0.0, 0.01)
+        np.testing.assert_allclose(acc, E * (q[sp] / m[sp])[:, None], rtol=tol, atol=tol)
+        np.testing.assert_allclose(ph, phi, rtol=tol)
+
+
+def test_kelbg_rejects_bad_params(U):
+    with pytest.raises(U.UcpError):
+        U.Context(16, (1.0, -1.0), (1000.0, 1.0), kelbg_lambda=0.0)
+    with pytest.raises(U.UcpError):
+        U.Context(16, (1.0, 1.0), (1000.0, 1.0), kelbg_lambda=0.1)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_sec5_relaxation_short_run(U, orc, prec):
+    """Sec. 5 set-up in reduced units (Wigner-Seitz radius of 4.32e9 cm^-3, T_e = 3 K,
+    T_i = 1e-6 K, ion mass 0.01 amu, dt = 20 fs, lambda_ei = 100 A): a short run of
+    the GPU tree against the direct-sum oracle, both with the Kelbg e-i law."""
+    from paper_0709_3331_gb300.inputs import sec5_units, uniform_sphere
+    u = sec5_units(4.32e9, 100.0, 3.0, 1e-6, 0.01, 20.0)
+    n = 1024
+    c = uniform_sphere(n, (n / 2) ** (1.0 / 3.0), 51, u["t_e"], u["t_i"], u["m_i"])
+    steps, k = 40, 1
+    with orc.kelbg(u["lambda"]):
+        p_ref, v_ref, _ = orc.run(c.pos, c.vel, c.species, c.q, c.m, u["dt"], k, steps // k,
+                                  0.5, 0.0, direct_sum=True, nthreads=4)
+    with U.Context(n, c.q, c.m, leaf_cap=8, precision=prec, kelbg_lambda=u["lambda"]) as ctx:
+        ctx.set_state(c.pos, c.vel, c.species)
+        ctx.step(u["dt"], k, steps, 0.3, 0.0)
+        pos, vel = ctx.get_state()
+    def temps(v):
+        ke = 0.5 * c.m[c.species] * (v ** 2).sum(1)
+        return [2 * ke[c.species == s].sum() / (3 * (c.species == s).sum()) for s in (0, 1)]
+    t_ref, t_gpu = temps(v_ref), temps(vel)
+    np.testing.assert_allclose(t_gpu, t_ref, rtol=1e-3)
+    assert np.abs(pos - p_ref).max() < 1e-6 * np.abs(c.pos).max()
