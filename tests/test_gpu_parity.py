@@ -357,7 +357,11 @@ def test_kelbg_coincident_pair(U, orc):
     q, m = np.array([1.0, -1.0]), np.array([1000.0, 1.0])
     with orc.kelbg(0.2):
         E, phi = orc.direct(pos, sp, q, 0.01)
-    for prec, tol in ((0, 1e-12), (1, 1e-5)):
+    # FP64 only: the Kelbg force keeps a finite magnitude q/(2 lambda^2) as r -> 0 with a
+    # direction set by the separation, so an exactly coincident pair (zero force by
+    # definition) is reproduced only where positions are differenced exactly; the FP32C
+    # node-relative offsets of a coincident pair differ by a rounding error
+    for prec, tol in ((0, 1e-12),):
         with U.Context(4, q, m, leaf_cap=1, precision=prec, kelbg_lambda=0.2) as ctx:
             ctx.set_state(pos, vel, sp)
             acc, ph = ctx.tree_force(0.0, 0.01)
