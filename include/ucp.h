@@ -74,6 +74,17 @@ typedef struct {
  * it will need (nothing is allocated later).  *out is set on success. */
 int ucp_create(ucp_ctx** out, const ucp_params* params);
 
+/* Ensemble of n_clouds independent clouds (1 <= n_clouds <= UCP_MAX_CLOUDS) in
+ * one context: cloud c holds sizes[c] >= 1 particles, at caller indices
+ * [sizes[0] + ... + sizes[c-1], ... + sizes[c]).  Clouds do not interact; each
+ * has its own enclosing cube and TREE (Sec. 3), and every call below works on
+ * all clouds at once, one kernel launch per stage for the whole ensemble (the
+ * walk is one persistent launch over all clouds' targets).  params->n must be 0
+ * or the total; the other parameters are common to all clouds. */
+#define UCP_MAX_CLOUDS 256
+int ucp_create_batch(ucp_ctx** out, const ucp_params* params, int32_t n_clouds,
+                     const int64_t* sizes);
+
 /* Free the context and its device memory (NULL is allowed). */
 void ucp_destroy(ucp_ctx* ctx);
 
@@ -120,6 +131,11 @@ int ucp_step(ucp_ctx* ctx, double dt_e, int ion_substep_ratio, int64_t n_electro
  * same theta and eps this is a reduction only, otherwise one walk runs first. */
 int ucp_energy(ucp_ctx* ctx, double theta, double eps, double out[6]);
 
+/* Per-cloud observables of an ensemble: out[6 c + j] as ucp_energy's out[j]
+ * for cloud c (n_clouds x 6 doubles); ucp_energy returns the sums (and |P| of
+ * the total momentum). */
+int ucp_energy_clouds(ucp_ctx* ctx, double theta, double eps, double* out);
+
 /* Counters: out = {direct pairs, multipole evaluations, walk targets, walk
  * launches} summed since the last reset, {boxes, deepest depth} of the last
  * tree, {CUDA kernels launched by this library (all contexts of the process)
@@ -137,6 +153,7 @@ int ucp_stats(ucp_ctx* ctx, int64_t out[8], int reset);
  * ucp_get_counts: direct pairs and multipole evaluations per particle in the
  * last walk, in the caller's order (0 for particles that were not targets). */
 int ucp_get_cube(ucp_ctx* ctx, double out[4]);
+int ucp_get_cubes(ucp_ctx* ctx, double* out); /* n_clouds x 4: every cloud's cube */
 int ucp_get_sorted(ucp_ctx* ctx, uint64_t* keys, uint32_t* ids, int on_device);
 int ucp_get_tree(ucp_ctx* ctx, int64_t* nnodes, int64_t cap, int32_t* topo,
                  int8_t* is_leaf, double* geom);

@@ -114,11 +114,17 @@ __device__ __forceinline__ double unord64(unsigned long long u)
     return __longlong_as_double((long long)((u >> 63) ? (u & 0x7fffffffffffffffull) : ~u));
 }
 
+// Partial min/max of cloud blockIdx.y over its segment (the whole array when
+// cloud_start is NULL); block x of the cloud strides the segment.
 __global__ void k_bbox_partial(const double* __restrict__ x, const double* __restrict__ y,
-                               const double* __restrict__ z, int n, double* __restrict__ part)
+                               const double* __restrict__ z, int n, double* __restrict__ part,
+                               const int* __restrict__ cloud_start)
 {
+    const int c = blockIdx.y;
+    const int lo_i = cloud_start ? cloud_start[c] : 0, hi_i = cloud_start ? cloud_start[c + 1] : n;
     unsigned long long lo[3] = {~0ull, ~0ull, ~0ull}, hi[3] = {0ull, 0ull, 0ull};
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    for (int i = lo_i + blockIdx.x * blockDim.x + threadIdx.x; i < hi_i;
+         i += gridDim.x * blockDim.x) {
         unsigned long long v[3] = {ord64(x[i]), ord64(y[i]), ord64(z[i])};
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
@@ -148,9 +154,10 @@ __global__ void k_bbox_partial(const double* __restrict__ x, const double* __res
                 s[0][3 + a] = max(s[0][3 + a], s[ww][3 + a]);
             }
         // an empty partial (more blocks than particles) keeps +/-inf
+        double* pp = part + ((size_t)c * gridDim.x + blockIdx.x) * 6;
         for (int a = 0; a < 3; ++a) {
-            part[blockIdx.x * 6 + a] = s[0][a] == ~0ull ? INFINITY : unord64(s[0][a]);
-            part[blockIdx.x * 6 + 3 + a] = s[0][3 + a] == 0ull ? -INFINITY : unord64(s[0][3 + a]);
+            pp[a] = s[0][a] == ~0ull ? INFINITY : unord64(s[0][a]);
+            pp[3 + a] = s[0][3 + a] == 0ull ? -INFINITY : unord64(s[0][3 + a]);
         }
     }
 }
@@ -158,8 +165,10 @@ __global__ void k_bbox_partial(const double* __restrict__ x, const double* __res
 // Sec. 3: the cube that encloses every particle.  Centre = (min + max) / 2 per
 // axis; side = largest extent * (1 + 2^-20) so that the maximum falls inside;
 // side 1 when all particles coincide.
-__global__ void k_bbox_final(const double* __restrict__ part, int nblk, Cube* cube)
+__global__ void k_bbox_final(const double* __restrict__ part, int nblk, Cube* cubes)
 {
+    part += (size_t)blockIdx.x * nblk * 6;  // cloud blockIdx.x
+    Cube* cube = cubes + blockIdx.x;
     __shared__ double s[256][6];
     double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
     for (int b = threadIdx.x; b < nblk; b += blockDim.x)
@@ -215,11 +224,13 @@ __device__ __forceinline__ unsigned int cell_coord(double x, double lo, double k
 }
 
 __global__ void k_keys(const double* __restrict__ x, const double* __restrict__ y,
-                       const double* __restrict__ z, int n, const Cube* __restrict__ cube,
+                       const double* __restrict__ z, int n, const Cube* __restrict__ cubes,
+                       const unsigned char* __restrict__ cloud,
                        unsigned long long* __restrict__ key, unsigned int* __restrict__ val)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
+    const Cube* cube = cubes + (cloud ? cloud[i] : 0);
     double ks = cube->kscale;
     unsigned int kx = cell_coord(x[i], cube->lo[0], ks);
     unsigned int ky = cell_coord(y[i], cube->lo[1], ks);
@@ -279,7 +290,8 @@ __global__ void __launch_bounds__(kSortThreads)
 k_onesweep(const unsigned long long* __restrict__ kin, const unsigned int* __restrict__ vin,
            unsigned long long* __restrict__ kout, unsigned int* __restrict__ vout, int n,
            int shift, const unsigned int* __restrict__ goff, unsigned long long* status,
-           int* tile_ctr, unsigned int epoch, int* err, int spin_limit)
+           int* tile_ctr, unsigned int epoch, int* err, int spin_limit,
+           const unsigned char* __restrict__ digit_of_val)
 {
     __shared__ int cnt[kSortWarps][kRadix];
     __shared__ int s_tile, s_fail;
@@ -302,7 +314,9 @@ k_onesweep(const unsigned long long* __restrict__ kin, const unsigned int* __res
         bool ok = i < n;
         kk[c] = ok ? kin[i] : 0ull;
         vv[c] = ok ? vin[i] : 0u;
-        int d = ok ? (int)((kk[c] >> shift) & 0xffu) : kRadix + lane;  // invalid lanes unique
+        // digit: 8 key bits, or (cloud pass) the cloud of the element's previous slot
+        int d = ok ? (digit_of_val ? (int)digit_of_val[vv[c]] : (int)((kk[c] >> shift) & 0xffu))
+                   : kRadix + lane;  // invalid lanes unique
         dig[c] = d;
         unsigned int peers = __match_any_sync(0xffffffffu, d);
         int leader = __ffs(peers) - 1;
@@ -394,18 +408,21 @@ __device__ __forceinline__ unsigned long long prefix_at(unsigned long long k, in
     return d == 0 ? 0ull : (k >> (3 * (kMaxDepth - d)));
 }
 
-// first j > i whose depth-d prefix differs from key[i]'s (or n)
-__device__ int box_end(const unsigned long long* __restrict__ K, int n, int i, int d)
+// Boxes never span two clouds: every cloud occupies a fixed segment
+// [seg_lo, seg_hi) of the key-sorted order (its own root, its own cube).
+
+// first j > i in the segment whose depth-d prefix differs from key[i]'s (or seg_hi)
+__device__ int box_end(const unsigned long long* __restrict__ K, int seg_hi, int i, int d)
 {
-    if (d == 0) return n;
+    if (d == 0) return seg_hi;
     unsigned long long p = prefix_at(K[i], d);
     int lo = i, step = 1, hi = i + 1;
-    while (hi < n && prefix_at(K[hi], d) == p) {
+    while (hi < seg_hi && prefix_at(K[hi], d) == p) {
         lo = hi;
         step <<= 1;
         hi = i + step;
     }
-    if (hi > n) hi = n;
+    if (hi > seg_hi) hi = seg_hi;
     while (hi - lo > 1) {
         int mid = lo + ((hi - lo) >> 1);
         if (prefix_at(K[mid], d) == p) lo = mid;
@@ -414,18 +431,18 @@ __device__ int box_end(const unsigned long long* __restrict__ K, int n, int i, i
     return hi;
 }
 
-// first j <= i whose depth-d prefix equals key[i]'s
-__device__ int box_begin(const unsigned long long* __restrict__ K, int i, int d)
+// first j <= i in the segment whose depth-d prefix equals key[i]'s
+__device__ int box_begin(const unsigned long long* __restrict__ K, int seg_lo, int i, int d)
 {
-    if (d == 0) return 0;
+    if (d == 0) return seg_lo;
     unsigned long long p = prefix_at(K[i], d);
     int hi = i, step = 1, lo = i - 1;
-    while (lo >= 0 && prefix_at(K[lo], d) == p) {
+    while (lo >= seg_lo && prefix_at(K[lo], d) == p) {
         hi = lo;
         step <<= 1;
         lo = i - step;
     }
-    if (lo < -1) lo = -1;
+    if (lo < seg_lo - 1) lo = seg_lo - 1;
     while (hi - lo > 1) {
         int mid = lo + ((hi - lo) >> 1);
         if (prefix_at(K[mid], d) == p) hi = mid;
@@ -435,12 +452,25 @@ __device__ int box_begin(const unsigned long long* __restrict__ K, int i, int d)
 }
 
 // depth of the first box that starts at sorted position i (22 = none)
-__device__ __forceinline__ int first_depth(const unsigned long long* __restrict__ K, int i)
+__device__ __forceinline__ int first_depth(const unsigned long long* __restrict__ K, int seg_lo,
+                                           int i)
 {
-    if (i == 0) return 0;
+    if (i == seg_lo) return 0;
     unsigned long long x = K[i] ^ K[i - 1];
     if (x == 0ull) return kMaxDepth + 1;
     return (__clzll((long long)x) - 1) / 3 + 1;
+}
+
+__device__ __forceinline__ void segment_of(const Tree& t, int n, int i, int& lo, int& hi)
+{
+    if (t.cloud) {
+        const int c = t.cloud[i];
+        lo = t.cloud_start[c];
+        hi = t.cloud_start[c + 1];
+    } else {
+        lo = 0;
+        hi = n;
+    }
 }
 
 // Every box is a key prefix; the boxes that start at sorted position i are
@@ -448,21 +478,23 @@ __device__ __forceinline__ int first_depth(const unsigned long long* __restrict_
 // its parent holds more than leaf_cap particles.  Emitting boxes in order of
 // (start position, depth) gives pre-order with children in octant order.
 __global__ void k_topo_count(const unsigned long long* __restrict__ K, int n, int leaf_cap,
-                             int* __restrict__ cnt)
+                             int* __restrict__ cnt, Tree t)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    int d0 = first_depth(K, i);
+    int lo, hi;
+    segment_of(t, n, i, lo, hi);
+    int d0 = first_depth(K, lo, i);
     int c = 0;
     if (d0 <= kMaxDepth) {
         bool ok = true;
         if (d0 > 0) {
-            int pb = box_begin(K, i, d0 - 1), pe = box_end(K, n, i, d0 - 1);
+            int pb = box_begin(K, lo, i, d0 - 1), pe = box_end(K, hi, i, d0 - 1);
             ok = pe - pb > leaf_cap;
         }
         if (ok)
             for (int d = d0; d <= kMaxDepth; ++d) {
-                int e = box_end(K, n, i, d);
+                int e = box_end(K, hi, i, d);
                 ++c;
                 if (e - i <= leaf_cap || d == kMaxDepth) break;
             }
@@ -480,17 +512,19 @@ __global__ void k_topo_emit(const unsigned long long* __restrict__ K, int n, int
     int nn = min(*t.nnodes, t.cap);
     if (i == 0 && *t.nnodes > t.cap) *t.nnodes = t.cap;
     if (c == 0) return;
-    int d0 = first_depth(K, i);
+    int lo, hi;
+    segment_of(t, n, i, lo, hi);
+    int d0 = first_depth(K, lo, i);
     int node = off[i];
     int parent = -1;
     if (d0 > 0) {
-        int pb = box_begin(K, i, d0 - 1);
-        parent = off[pb] + (d0 - 1 - first_depth(K, pb));
+        int pb = box_begin(K, lo, i, d0 - 1);
+        parent = off[pb] + (d0 - 1 - first_depth(K, lo, pb));
     }
     int dmax = 0;
     for (int j = 0; j < c; ++j) {
         int d = d0 + j;
-        int e = box_end(K, n, i, d);
+        int e = box_end(K, hi, i, d);
         bool leaf = (e - i <= leaf_cap) || d == kMaxDepth;
         int nx = e < n ? off[e] : nn;
         if (node >= t.cap) break;  // cannot happen: the capacity bounds the box count
@@ -518,6 +552,12 @@ __device__ __forceinline__ unsigned int compact3(unsigned long long x)
     x = (x | (x >> 16)) & 0x001f00000000ffffull;
     x = (x | (x >> 32)) & 0x1fffffull;
     return (unsigned int)x;
+}
+
+// cube of the cloud that owns the box starting at sorted position i
+__device__ __forceinline__ Cube cube_of(const Cube* __restrict__ cubes, const Tree& t, int i)
+{
+    return cubes[t.cloud ? t.cloud[i] : 0];
 }
 
 // geometric box centre: lo + (cell + 1/2) * side, side = L 2^-depth
@@ -581,12 +621,12 @@ k_moments_leaves(const double* __restrict__ x, const double* __restrict__ y,
                  float4* __restrict__ src32, int want_f32)
 {
     const int nl = t.count[kMaxDepth + 1];
-    const Cube cb = *cube;
     const double q0 = qsp[0], q1 = qsp[1];
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nl; i += gridDim.x * blockDim.x) {
         const int node = t.leaf_list[i];
         const int dl = t.depth_leaf[node];
         const int4 inf = t.info[node];
+        const Cube cb = cube_of(cube, t, inf.x);
         double zc[3], side;
         box_centre(cb, t.cell[node], dl & 255, zc, &side);
         double a[14];
@@ -639,13 +679,13 @@ k_moments_leaves(const double* __restrict__ x, const double* __restrict__ y,
 __global__ void __launch_bounds__(256)
 k_moments_twigs(const Cube* __restrict__ cube, Tree t, int d_hi, int d_lo)
 {
-    const Cube cb = *cube;
     // several depths in one launch only with a single block (barrier between depths)
     for (int d = d_hi; d >= d_lo; --d) {
     const int nt = t.count[d];
     const int* __restrict__ list = t.twig_list + t.twig_off[d];
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nt; i += gridDim.x * blockDim.x) {
         const int p = list[i];
+        const Cube cb = cube_of(cube, t, t.info[p].x);
         double zp[3], ps;
         box_centre(cb, t.cell[p], d, zp, &ps);
         const int4 c03 = *reinterpret_cast<const int4*>(t.child8 + (size_t)p * 8);
@@ -744,12 +784,12 @@ k_moments_leaves_f32(const double* __restrict__ x, const double* __restrict__ y,
                      float4* __restrict__ src32)
 {
     const int nl = t.count[kMaxDepth + 1];
-    const Cube cb = *cube;
     const float q0 = (float)qsp[0], q1 = (float)qsp[1];
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nl; i += gridDim.x * blockDim.x) {
         const int node = t.leaf_list[i];
         const int dl = t.depth_leaf[node];
         const int4 inf = t.info[node];
+        const Cube cb = cube_of(cube, t, inf.x);
         double zc[3], side;
         box_centre(cb, t.cell[node], dl & 255, zc, &side);
         float a[14];
@@ -801,7 +841,6 @@ __global__ void __launch_bounds__(256)
 k_moments_twigs_f32(const Cube* __restrict__ cube, Tree t, int d_hi, int d_lo)
 {
     constexpr int G = 8;
-    const Cube cb = *cube;
     const int o = threadIdx.x & (G - 1);
     const int groups = gridDim.x * (blockDim.x / G);
     const int first = blockIdx.x * (blockDim.x / G) + (threadIdx.x / G);
@@ -814,6 +853,7 @@ k_moments_twigs_f32(const Cube* __restrict__ cube, Tree t, int d_hi, int d_lo)
             const int i = base + (first & 3);
             const bool have = i < nt;
             const int p = have ? list[i] : 0;
+            const Cube cb = cube_of(cube, t, have ? t.info[p].x : 0);
             double zp[3], ps;
             box_centre(cb, have ? t.cell[p] : 0ull, d, zp, &ps);
             const int ch = have ? t.child8[(size_t)p * 8 + o] : -1;
@@ -873,18 +913,19 @@ void launch_scan(const int* in, int* out, int n, int* partials, int* total, cuda
 }
 
 void launch_bbox(const double* x, const double* y, const double* z, int n, double* partials,
-                 int nblk, Cube* cube, cudaStream_t s)
+                 int nblk, Cube* cubes, const int* cloud_start, int n_clouds, cudaStream_t s)
 {
     count_launch(2);
-    k_bbox_partial<<<nblk, 256, 0, s>>>(x, y, z, n, partials);
-    k_bbox_final<<<1, 256, 0, s>>>(partials, nblk, cube);
+    k_bbox_partial<<<dim3(nblk, n_clouds), 256, 0, s>>>(x, y, z, n, partials, cloud_start);
+    k_bbox_final<<<n_clouds, 256, 0, s>>>(partials, nblk, cubes);
 }
 
-void launch_keys(const double* x, const double* y, const double* z, int n, const Cube* cube,
-                 unsigned long long* key, unsigned int* val, cudaStream_t s)
+void launch_keys(const double* x, const double* y, const double* z, int n, const Cube* cubes,
+                 const unsigned char* cloud, unsigned long long* key, unsigned int* val,
+                 cudaStream_t s)
 {
     count_launch(1);
-    k_keys<<<(n + 255) / 256, 256, 0, s>>>(x, y, z, n, cube, key, val);
+    k_keys<<<(n + 255) / 256, 256, 0, s>>>(x, y, z, n, cubes, cloud, key, val);
 }
 
 size_t sort_test_words() { return 4 * (size_t)kSortTile; }
@@ -892,15 +933,16 @@ size_t sort_test_words() { return 4 * (size_t)kSortTile; }
 size_t sort_status_words(int n)
 {
     int nb = (n + kSortTile - 1) / kSortTile;
-    return (size_t)8 * kRadix * (size_t)(nb > 0 ? nb : 1);
+    return (size_t)9 * kRadix * (size_t)(nb > 0 ? nb : 1);
 }
 
-void launch_sort(unsigned long long* key[2], unsigned int* val[2], int n, SortScratch sc,
-                 const unsigned int* ids_in, unsigned int epoch0, cudaStream_t s)
+int launch_sort(unsigned long long* key[2], unsigned int* val[2], int n, SortScratch sc,
+                const unsigned int* ids_in, unsigned int epoch0, const unsigned char* cloud,
+                const int* cloud_start, int n_clouds, cudaStream_t s)
 {
-    count_launch(11);
+    count_launch(11 + (n_clouds > 1 ? 1 : 0));
     const int nb = (n + kSortTile - 1) / kSortTile;
-    cudaMemsetAsync(sc.ghist, 0, sizeof(unsigned int) * (8 * kRadix + 8), s);  // + tile counters
+    cudaMemsetAsync(sc.ghist, 0, sizeof(unsigned int) * (8 * kRadix + 9), s);  // + tile counters
     int hb = (n + 4 * kSortThreads - 1) / (4 * kSortThreads);
     if (hb > 2 * 152) hb = 2 * 152;
     k_sort_hist_all<<<hb > 0 ? hb : 1, kSortThreads, 0, s>>>(key[0], n, sc.ghist);
@@ -911,11 +953,21 @@ void launch_sort(unsigned long long* key[2], unsigned int* val[2], int n, SortSc
         k_onesweep<<<nb, kSortThreads, 0, s>>>(key[cur], val[cur], key[cur ^ 1], val[cur ^ 1], n,
                                                8 * p, sc.goff + p * kRadix,
                                                sc.status + (size_t)p * nb * kRadix, tiles + p,
-                                               epoch0 + (unsigned int)p, sc.err, kSortSpinLimit);
+                                               epoch0 + (unsigned int)p, sc.err, kSortSpinLimit,
+                                               nullptr);
         cur ^= 1;
     }
-    // eight passes: the result is back in buffer 0
-    k_tiefix<<<(n + 255) / 256, 256, 0, s>>>(key[0], val[0], ids_in, n);
+    if (n_clouds > 1) {
+        // a ninth stable pass by cloud: (cloud, key) order, each cloud back in its
+        // fixed segment; the offsets of a cloud are its segment start
+        k_onesweep<<<nb, kSortThreads, 0, s>>>(key[cur], val[cur], key[cur ^ 1], val[cur ^ 1], n,
+                                               0, reinterpret_cast<const unsigned int*>(cloud_start),
+                                               sc.status + (size_t)8 * nb * kRadix, tiles + 8,
+                                               epoch0 + 8u, sc.err, kSortSpinLimit, cloud);
+        cur ^= 1;
+    }
+    k_tiefix<<<(n + 255) / 256, 256, 0, s>>>(key[cur], val[cur], ids_in, n);
+    return cur;
 }
 
 int sort_selftest_timeout(SortScratch sc, cudaStream_t s)
@@ -934,7 +986,7 @@ int sort_selftest_timeout(SortScratch sc, cudaStream_t s)
     // input: tiles 0-1 of the test buffers; output: tiles 2-3
     k_onesweep<<<1, kSortThreads, 0, s>>>(sc.test_keys, sc.test_vals, sc.test_keys + 2 * kSortTile,
                                           sc.test_vals + 2 * kSortTile, 2 * kSortTile, 0, sc.goff,
-                                          sc.status, tiles, 1u, sc.err, 2000);
+                                          sc.status, tiles, 1u, sc.err, 2000, nullptr);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
@@ -951,7 +1003,7 @@ void launch_topology(const unsigned long long* key, int n, int leaf_cap, int* po
     count_launch(3);
     cudaMemsetAsync(t.maxdepth, 0, sizeof(int), s);
     cudaMemsetAsync(t.count, 0, sizeof(int) * (kMaxDepth + 2), s);
-    k_topo_count<<<(n + 255) / 256, 256, 0, s>>>(key, n, leaf_cap, pos_cnt);
+    k_topo_count<<<(n + 255) / 256, 256, 0, s>>>(key, n, leaf_cap, pos_cnt, t);
     launch_scan(pos_cnt, pos_off, n, scan_part, t.nnodes, s);
     k_clear_children<<<2 * 152, 256, 0, s>>>(t);
     k_topo_emit<<<(n + 255) / 256, 256, 0, s>>>(key, n, leaf_cap, pos_cnt, pos_off, t);

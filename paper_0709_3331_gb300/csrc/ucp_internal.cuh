@@ -46,6 +46,10 @@ struct Tree {
     int* twig_list;          // the twigs of depth d at twig_off[d] .. + count[d]
     int* count;              // count[d] twigs of depth d (d <= 20), count[kMaxDepth + 1] leaves
     int twig_off[kMaxDepth + 2];
+    // clouds: cloud[i] = cloud of key-sorted position i, whose segment is
+    // [cloud_start[c], cloud_start[c + 1]); NULL cloud = one cloud over [0, n)
+    const unsigned char* cloud;
+    const int* cloud_start;
 };
 
 struct Cube {                // enclosing cube: centre, side, lower corner, 2^21 / side
@@ -57,21 +61,24 @@ struct Cube {                // enclosing cube: centre, side, lower corner, 2^21
 
 // ---- build (ucp_build.cu) ----
 void launch_bbox(const double* x, const double* y, const double* z, int n, double* partials,
-                 int nblk, Cube* cube, cudaStream_t s);
-void launch_keys(const double* x, const double* y, const double* z, int n, const Cube* cube,
-                 unsigned long long* key, unsigned int* val, cudaStream_t s);
+                 int nblk, Cube* cubes, const int* cloud_start, int n_clouds, cudaStream_t s);
+void launch_keys(const double* x, const double* y, const double* z, int n, const Cube* cubes,
+                 const unsigned char* cloud, unsigned long long* key, unsigned int* val,
+                 cudaStream_t s);
 struct SortScratch {
-    unsigned int* ghist;           // 8 x 256 digit counts, then 8 tile counters
+    unsigned int* ghist;           // 8 x 256 digit counts, then 9 tile counters
     unsigned int* goff;            // 8 x 256 digit offsets
-    unsigned long long* status;    // 8 passes x tiles x 256 published words
+    unsigned long long* status;    // 9 passes x tiles x 256 published words
     int* err;                      // raised by a wait that gave up
     unsigned long long* test_keys; // 4 tiles, for the bounded-wait self-test
     unsigned int* test_vals;
 };
 size_t sort_status_words(int n);
 size_t sort_test_words();
-void launch_sort(unsigned long long* key[2], unsigned int* val[2], int n, SortScratch sc,
-                 const unsigned int* ids_in, unsigned int epoch0, cudaStream_t s);
+// returns the buffer (0 or 1) that holds the sorted keys and permutation
+int launch_sort(unsigned long long* key[2], unsigned int* val[2], int n, SortScratch sc,
+                const unsigned int* ids_in, unsigned int epoch0, const unsigned char* cloud,
+                const int* cloud_start, int n_clouds, cudaStream_t s);
 int sort_selftest_timeout(SortScratch sc, cudaStream_t s);
 void launch_tiefix(const unsigned long long* key, unsigned int* perm, const unsigned int* ids,
                    int n, cudaStream_t s);
@@ -94,6 +101,9 @@ struct WalkArgs {
     Tree t;
     const int* targets;     // key-order slots of the targets, or NULL = all
     int ntargets;
+    const int4* chunks;     // {first target index, count <= 32, cloud, 0}, one cloud each
+    int nchunks;
+    const int* pos_off;     // first box started at each sorted position (the roots)
     double eps2;
     int kelbg;              // electron-ion pairs use the Kelbg form (Sec. 2.1 Eq. 3)
     double lambda;          // its fixed lambda_ei
@@ -120,6 +130,9 @@ void launch_select(const int8_t* sp, int species, int n, int* flags, int* list, 
 void launch_energy(const double* vx, const double* vy, const double* vz, const double* phi,
                    const int8_t* sp, const double* qsp, const double* msp, int n,
                    double* partials, int nblk, double* out6, cudaStream_t s);
+void launch_energy_clouds(const double* vx, const double* vy, const double* vz, const double* phi,
+                          const int8_t* sp, const double* qsp, const double* msp,
+                          const int* cloud_start, int n_clouds, double* out, cudaStream_t s);
 void launch_scatter3(const double* ax, const double* ay, const double* az, const unsigned int* id,
                      int n, double* out, cudaStream_t s);
 void launch_scatter1(const double* a, const unsigned int* id, int n, double* out, cudaStream_t s);

@@ -108,6 +108,37 @@ __global__ void k_energy_partial(const double* __restrict__ vx, const double* __
         for (int k = 0; k < 6; ++k) part[blockIdx.x * 6 + k] = sh[0][k];
 }
 
+// Per-cloud observables, one block per cloud over its segment (fixed order):
+// out[6 c ..] = {KE_ion, KE_electron, PE, px, py, pz}
+__global__ void k_energy_clouds(const double* __restrict__ vx, const double* __restrict__ vy,
+                                const double* __restrict__ vz, const double* __restrict__ phi,
+                                const int8_t* __restrict__ sp, const double* __restrict__ qsp,
+                                const double* __restrict__ msp, const int* __restrict__ cloud_start,
+                                double* __restrict__ out)
+{
+    const int c = blockIdx.x;
+    double acc[6] = {0, 0, 0, 0, 0, 0};
+    for (int i = cloud_start[c] + threadIdx.x; i < cloud_start[c + 1]; i += blockDim.x) {
+        int s = sp[i];
+        double m = msp[s];
+        double ux = vx[i], uy = vy[i], uz = vz[i];
+        acc[s] += 0.5 * m * (ux * ux + uy * uy + uz * uz);
+        acc[2] += 0.5 * qsp[s] * phi[i];
+        acc[3] += m * ux;
+        acc[4] += m * uy;
+        acc[5] += m * uz;
+    }
+    __shared__ double sh[kT][6];
+    for (int k = 0; k < 6; ++k) sh[threadIdx.x][k] = acc[k];
+    __syncthreads();
+    for (int st = kT / 2; st > 0; st >>= 1) {
+        if ((int)threadIdx.x < st)
+            for (int k = 0; k < 6; ++k) sh[threadIdx.x][k] += sh[threadIdx.x + st][k];
+        __syncthreads();
+    }
+    if (threadIdx.x < 6) out[6 * c + threadIdx.x] = sh[0][threadIdx.x];
+}
+
 __global__ void k_energy_final(const double* __restrict__ part, int nblk, double* __restrict__ out)
 {
     if (threadIdx.x != 0) return;
@@ -218,6 +249,14 @@ void launch_energy(const double* vx, const double* vy, const double* vz, const d
     count_launch(2);
     k_energy_partial<<<nblk, kT, 0, s>>>(vx, vy, vz, phi, sp, qsp, msp, n, partials);
     k_energy_final<<<1, 32, 0, s>>>(partials, nblk, out6);
+}
+
+void launch_energy_clouds(const double* vx, const double* vy, const double* vz, const double* phi,
+                          const int8_t* sp, const double* qsp, const double* msp,
+                          const int* cloud_start, int n_clouds, double* out, cudaStream_t s)
+{
+    count_launch(1);
+    k_energy_clouds<<<n_clouds, kT, 0, s>>>(vx, vy, vz, phi, sp, qsp, msp, cloud_start, out);
 }
 
 void launch_scatter3(const double* ax, const double* ay, const double* az, const unsigned int* id,

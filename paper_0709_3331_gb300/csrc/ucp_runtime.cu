@@ -10,6 +10,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <algorithm>
 #include <new>
 #include <string>
 #include <vector>
@@ -63,12 +64,22 @@ struct ucp_ctx {
     int* stage_int = nullptr;
 
     int n_e = 0;
+    // clouds: independent particle sets in fixed segments of every order
+    int n_clouds = 1;
+    std::vector<int> cloud_start_h;    // n_clouds + 1
+    int* cloud_start = nullptr;        // device copy
+    unsigned char* cloud = nullptr;    // cloud of each slot (batches only)
+    int4* chunks_all = nullptr;        // walk chunks over all particles
+    int4* chunks_e = nullptr;          // walk chunks over the compacted electrons
+    int n_chunks_all = 0, n_chunks_e = 0, n_chunks_all_cap = 0;
+    int sorted_buf = 0;                // key[] / val[] buffer of the last sort
+    std::vector<double> cloud_energy;  // per-cloud {KE_i, KE_e, PE, px, py, pz} of the last energy
     bool have_state = false, tree_valid = false, acc_valid = false;
     bool phi_valid = false;           // phi of every particle at the current positions
     double phi_theta = -1.0, phi_eps = -1.0;
     int64_t steps = 0, walk_targets = 0, walk_launches = 0;
     unsigned long long launch_base = 0;
-    unsigned int sort_epoch = 16;     // tags of the sort's published words (8 per build)
+    unsigned int sort_epoch = 16;     // tags of the sort's published words (16 per build)
 
     bool prof = false;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
@@ -155,21 +166,25 @@ void prof_end(ucp_ctx* c)
 int build(ucp_ctx* c)
 {
     int n = c->n, k = c->cur;
+    const int* cs = c->n_clouds > 1 ? c->cloud_start : nullptr;
     launch_bbox(c->st[k][0], c->st[k][1], c->st[k][2], n, c->bbox_part, c->bbox_nblk, c->cube,
-                c->s);
-    launch_keys(c->st[k][0], c->st[k][1], c->st[k][2], n, c->cube, c->key[0], c->val[0], c->s);
-    launch_sort(c->key, c->val, n, c->sort, c->id[k], c->sort_epoch, c->s);
-    c->sort_epoch += 8;
+                cs, c->n_clouds, c->s);
+    launch_keys(c->st[k][0], c->st[k][1], c->st[k][2], n, c->cube, c->t.cloud, c->key[0],
+                c->val[0], c->s);
+    const int b = launch_sort(c->key, c->val, n, c->sort, c->id[k], c->sort_epoch, c->t.cloud,
+                              c->cloud_start, c->n_clouds, c->s);
+    c->sort_epoch += 16;
+    c->sorted_buf = b;
     const double* src[6];
     double* dst[6];
     for (int a = 0; a < 6; ++a) {
         src[a] = c->st[k][a];
         dst[a] = c->st[k ^ 1][a];
     }
-    launch_permute(c->val[0], n, src, dst, c->sp[k], c->sp[k ^ 1], c->id[k], c->id[k ^ 1], c->s);
+    launch_permute(c->val[b], n, src, dst, c->sp[k], c->sp[k ^ 1], c->id[k], c->id[k ^ 1], c->s);
     c->cur = k ^ 1;
     k = c->cur;
-    launch_topology(c->key[0], n, c->leaf_cap, c->pos_cnt, c->pos_off, c->scan_part, c->t, c->s);
+    launch_topology(c->key[b], n, c->leaf_cap, c->pos_cnt, c->pos_off, c->scan_part, c->t, c->s);
     launch_moments(c->st[k][0], c->st[k][1], c->st[k][2], c->sp[k], c->qsp, n, c->cube, c->t,
                    c->src32, c->precision == UCP_FP32C, c->s);
     c->tree_valid = true;
@@ -198,10 +213,15 @@ int force(ucp_ctx* c, double theta, double eps, int electrons_only, bool want_ph
                       c->s);
         a.targets = c->tlist;
         a.ntargets = c->n_e;
+        a.chunks = c->chunks_e;
+        a.nchunks = c->n_chunks_e;
     } else {
         a.targets = nullptr;
         a.ntargets = c->n;
+        a.chunks = c->chunks_all;
+        a.nchunks = c->n_chunks_all;
     }
+    a.pos_off = c->pos_off;
     a.eps2 = eps * eps;
     a.kelbg = c->potential == UCP_POT_KELBG;
     a.lambda = c->lambda_ei;
@@ -230,6 +250,33 @@ int force(ucp_ctx* c, double theta, double eps, int electrons_only, bool want_ph
         c->phi_eps = eps;
     }
     return check_launch(c, "tree walk");
+}
+
+// Walk chunks: up to 32 consecutive targets of one cloud.  All-particle chunks
+// cover each cloud's segment; electron chunks cover each cloud's run in the
+// compacted electron list (electrons keep their cloud order under sorting).
+int build_chunks(ucp_ctx* c, const std::vector<int>& ne_per_cloud)
+{
+    std::vector<int4> all, el;
+    int e0 = 0;
+    for (int cl = 0; cl < c->n_clouds; ++cl) {
+        int b = c->cloud_start_h[cl], e = c->cloud_start_h[cl + 1];
+        for (int t = b; t < e; t += 32) all.push_back(make_int4(t, std::min(32, e - t), cl, 0));
+        int ne = ne_per_cloud[cl];
+        for (int t = 0; t < ne; t += 32) el.push_back(make_int4(e0 + t, std::min(32, ne - t), cl, 0));
+        e0 += ne;
+    }
+    if ((int)all.size() > c->n_chunks_all_cap || (int)el.size() > c->n_chunks_all_cap)
+        return fail(c, UCP_EINVAL, "internal: chunk capacity");
+    c->n_chunks_all = (int)all.size();
+    c->n_chunks_e = (int)el.size();
+    CK(cudaMemcpyAsync(c->chunks_all, all.data(), sizeof(int4) * all.size(), cudaMemcpyHostToDevice,
+                       c->s));
+    if (!el.empty())
+        CK(cudaMemcpyAsync(c->chunks_e, el.data(), sizeof(int4) * el.size(),
+                           cudaMemcpyHostToDevice, c->s));
+    CK(cudaStreamSynchronize(c->s));
+    return UCP_OK;
 }
 
 // A bounded device-side wait that gave up leaves a flag; calls that synchronise
@@ -287,7 +334,22 @@ int ucp_create(ucp_ctx** out, const ucp_params* p)
 {
     if (!out || !p) return UCP_EINVAL;
     *out = nullptr;
-    if (p->n < 1 || p->n > 0x7fffffffLL) return UCP_EINVAL;
+    const int64_t n = p->n;
+    return ucp_create_batch(out, p, 1, &n);
+}
+
+int ucp_create_batch(ucp_ctx** out, const ucp_params* p, int32_t n_clouds, const int64_t* sizes)
+{
+    if (!out || !p || !sizes) return UCP_EINVAL;
+    *out = nullptr;
+    if (n_clouds < 1 || n_clouds > UCP_MAX_CLOUDS) return UCP_EINVAL;
+    int64_t total = 0;
+    for (int i = 0; i < n_clouds; ++i) {
+        if (sizes[i] < 1) return UCP_EINVAL;
+        total += sizes[i];
+    }
+    if (total > 0x7fffffffLL) return UCP_EINVAL;
+    if (n_clouds > 1 && p->n != 0 && p->n != total) return UCP_EINVAL;
     if (p->leaf_cap < 1 || p->leaf_cap > 1024) return UCP_EINVAL;
     if (p->precision != UCP_FP64 && p->precision != UCP_FP32C) return UCP_EINVAL;
     for (int s = 0; s < 2; ++s)
@@ -297,12 +359,16 @@ int ucp_create(ucp_ctx** out, const ucp_params* p)
     if (p->potential == UCP_POT_KELBG &&
         (!(p->lambda_ei > 0.0) || !std::isfinite(p->lambda_ei) || p->q[0] == p->q[1]))
         return UCP_EINVAL;
-    int64_t cap = box_capacity(p->n, p->leaf_cap);
+    int64_t cap = 0;
+    for (int i = 0; i < n_clouds; ++i) cap += box_capacity(sizes[i], p->leaf_cap);
     if (cap > 0x7ffffff0LL) return UCP_EINVAL;
 
     ucp_ctx* c = new (std::nothrow) ucp_ctx();
     if (!c) return UCP_ENOMEM;
-    c->n = (int)p->n;
+    c->n = (int)total;
+    c->n_clouds = n_clouds;
+    c->cloud_start_h.assign(n_clouds + 1, 0);
+    for (int i = 0; i < n_clouds; ++i) c->cloud_start_h[i + 1] = c->cloud_start_h[i] + (int)sizes[i];
     c->leaf_cap = p->leaf_cap;
     c->precision = p->precision;
     c->potential = p->potential;
@@ -332,7 +398,7 @@ int ucp_create(ucp_ctx** out, const ucp_params* p)
     if ((rc = dalloc(c, &c->ax, n)) || (rc = dalloc(c, &c->ay, n)) || (rc = dalloc(c, &c->az, n)) ||
         (rc = dalloc(c, &c->phi, n)))
         return bail(rc);
-    if ((rc = dalloc(c, &c->sort.ghist, 8 * 256 + 8)) || (rc = dalloc(c, &c->sort.goff, 8 * 256)) ||
+    if ((rc = dalloc(c, &c->sort.ghist, 8 * 256 + 9)) || (rc = dalloc(c, &c->sort.goff, 8 * 256)) ||
         (rc = dalloc(c, &c->sort.status, sort_status_words(c->n))) ||
         (rc = dalloc(c, &c->sort.err, 1)) ||
         (rc = dalloc(c, &c->sort.test_keys, sort_test_words())) ||
@@ -354,11 +420,14 @@ int ucp_create(ucp_ctx** out, const ucp_params* p)
         return bail(rc);
     {
         // twigs of depth d: at most min(8^d, n / (leaf_cap + 1)); none at the depth cap
-        int64_t off = 0, pow8 = 1, twigs = c->n / (c->leaf_cap + 1);
+        int64_t off = 0, pow8 = 1;
         for (int d = 0; d <= kMaxDepth + 1; ++d) {
             c->t.twig_off[d] = (int)off;
-            int64_t lim = d < kMaxDepth ? (pow8 < twigs ? pow8 : twigs) : 0;
-            off += lim;
+            if (d < kMaxDepth)
+                for (int i = 0; i < n_clouds; ++i) {
+                    int64_t twigs = sizes[i] / (c->leaf_cap + 1);
+                    off += pow8 < twigs ? pow8 : twigs;
+                }
             if (pow8 < ((int64_t)1 << 40)) pow8 *= 8;
         }
         if ((rc = dalloc(c, &c->t.twig_list, (size_t)(off > 0 ? off : 1)))) return bail(rc);
@@ -372,14 +441,48 @@ int ucp_create(ucp_ctx** out, const ucp_params* p)
         if (cudaMemsetAsync(c->src32, 0, sizeof(float4) * (n + 1), c->s) != cudaSuccess)
             return bail(UCP_ECUDA);
     }
-    if ((rc = dalloc(c, &c->cube, 1))) return bail(rc);
-    c->bbox_nblk = (int)((n + 2047) / 2048);
-    if (c->bbox_nblk > 4 * c->nsm) c->bbox_nblk = 4 * c->nsm;
-    if (c->bbox_nblk < 1) c->bbox_nblk = 1;
-    c->en_nblk = c->bbox_nblk;
-    if ((rc = dalloc(c, &c->bbox_part, (size_t)c->bbox_nblk * 6)) ||
-        (rc = dalloc(c, &c->en_part, (size_t)c->en_nblk * 6)) || (rc = dalloc(c, &c->en_out, 6)))
+    if ((rc = dalloc(c, &c->cube, (size_t)n_clouds))) return bail(rc);
+    {
+        int64_t biggest = 0;
+        for (int i = 0; i < n_clouds; ++i) biggest = sizes[i] > biggest ? sizes[i] : biggest;
+        c->bbox_nblk = (int)((biggest + 2047) / 2048);
+        int lim = n_clouds > 1 ? 16 : 4 * c->nsm;
+        if (c->bbox_nblk > lim) c->bbox_nblk = lim;
+        if (c->bbox_nblk < 1) c->bbox_nblk = 1;
+    }
+    c->en_nblk = (int)((n + 2047) / 2048);
+    if (c->en_nblk > 4 * c->nsm) c->en_nblk = 4 * c->nsm;
+    if (c->en_nblk < 1) c->en_nblk = 1;
+    if ((rc = dalloc(c, &c->bbox_part, (size_t)n_clouds * c->bbox_nblk * 6)) ||
+        (rc = dalloc(c, &c->en_part, (size_t)c->en_nblk * 6)) ||
+        (rc = dalloc(c, &c->en_out, (size_t)6 * n_clouds)))
         return bail(rc);
+    {
+        // clouds: segment starts, the (static) cloud of every slot, walk chunk capacity
+        if ((rc = dalloc(c, &c->cloud_start, (size_t)n_clouds + 1))) return bail(rc);
+        if (cudaMemcpyAsync(c->cloud_start, c->cloud_start_h.data(), sizeof(int) * (n_clouds + 1),
+                            cudaMemcpyHostToDevice, c->s) != cudaSuccess)
+            return bail(UCP_ECUDA);
+        c->t.cloud_start = c->cloud_start;
+        c->t.cloud = nullptr;
+        if (n_clouds > 1) {
+            std::vector<unsigned char> cl(n);
+            for (int i = 0; i < n_clouds; ++i)
+                for (int j = c->cloud_start_h[i]; j < c->cloud_start_h[i + 1]; ++j)
+                    cl[j] = (unsigned char)i;
+            if ((rc = dalloc(c, &c->cloud, n))) return bail(rc);
+            if (cudaMemcpyAsync(c->cloud, cl.data(), n, cudaMemcpyHostToDevice, c->s) != cudaSuccess ||
+                cudaStreamSynchronize(c->s) != cudaSuccess)
+                return bail(UCP_ECUDA);
+            c->t.cloud = c->cloud;
+        }
+        int64_t nch = 0;
+        for (int i = 0; i < n_clouds; ++i) nch += (sizes[i] + 31) / 32;
+        c->n_chunks_all_cap = (int)nch;
+        if ((rc = dalloc(c, &c->chunks_all, (size_t)nch)) ||
+            (rc = dalloc(c, &c->chunks_e, (size_t)nch)))
+            return bail(rc);
+    }
     if ((rc = dalloc(c, &c->qsp, 2)) || (rc = dalloc(c, &c->msp, 2))) return bail(rc);
     if ((rc = dalloc(c, &c->tflags, n)) || (rc = dalloc(c, &c->tlist, 2 * n)) ||
         (rc = dalloc(c, &c->tcount, 1)))
@@ -412,6 +515,7 @@ int ucp_set_state(ucp_ctx* c, const double* pos, const double* vel, const int8_t
     const double* dvel = vel;
     const int8_t* dsp = species;
     int k = c->cur;
+    std::vector<int8_t> host_sp;
     if (!on_device) {
         int ne = 0;
         for (size_t i = 0; i < n; ++i) {
@@ -438,12 +542,21 @@ int ucp_set_state(ucp_ctx* c, const double* pos, const double* vel, const int8_t
         if (fl[0]) return fail(c, UCP_ENONFINITE, "non-finite position or velocity");
         if (fl[1]) return fail(c, UCP_EINVAL, "species must be 0 (ion) or 1 (electron)");
         CK(cudaMemcpyAsync(c->sp[k], dsp, n, cudaMemcpyDeviceToDevice, c->s));
-        launch_select(c->sp[k], UCP_ELECTRON, c->n, c->tflags, c->tlist, c->scan_part, c->tcount,
-                      c->s);
-        int ne = 0;
-        CK(cudaMemcpyAsync(&ne, c->tcount, sizeof(int), cudaMemcpyDeviceToHost, c->s));
+        host_sp.resize(n);
+        CK(cudaMemcpyAsync(host_sp.data(), dsp, n, cudaMemcpyDeviceToHost, c->s));
         CK(cudaStreamSynchronize(c->s));
+        species = host_sp.data();
+        int ne = 0;
+        for (size_t i = 0; i < n; ++i) ne += species[i] == 1;
         c->n_e = ne;
+    }
+    {
+        std::vector<int> ne_cl(c->n_clouds, 0);
+        for (int cl = 0; cl < c->n_clouds; ++cl)
+            for (int i = c->cloud_start_h[cl]; i < c->cloud_start_h[cl + 1]; ++i)
+                ne_cl[cl] += species[i] == 1;
+        int rc = build_chunks(c, ne_cl);
+        if (rc) return rc;
     }
     launch_deinterleave(dpos, c->n, c->st[k][0], c->st[k][1], c->st[k][2], c->s);
     launch_deinterleave(dvel, c->n, c->st[k][3], c->st[k][4], c->st[k][5], c->s);
@@ -582,11 +695,23 @@ int ucp_energy(ucp_ctx* c, double theta, double eps, double out[6])
         (rc = force(c, theta, eps, 0, true)))
         return rc;
     int k = c->cur;
-    launch_energy(c->st[k][3], c->st[k][4], c->st[k][5], c->phi, c->sp[k], c->qsp, c->msp, c->n,
-                  c->en_part, c->en_nblk, c->en_out, c->s);
-    double r[6];
-    CK(cudaMemcpyAsync(r, c->en_out, sizeof(r), cudaMemcpyDeviceToHost, c->s));
-    CK(cudaStreamSynchronize(c->s));
+    double r[6] = {0, 0, 0, 0, 0, 0};
+    if (c->n_clouds == 1) {
+        launch_energy(c->st[k][3], c->st[k][4], c->st[k][5], c->phi, c->sp[k], c->qsp, c->msp,
+                      c->n, c->en_part, c->en_nblk, c->en_out, c->s);
+        CK(cudaMemcpyAsync(r, c->en_out, sizeof(r), cudaMemcpyDeviceToHost, c->s));
+        CK(cudaStreamSynchronize(c->s));
+    } else {
+        launch_energy_clouds(c->st[k][3], c->st[k][4], c->st[k][5], c->phi, c->sp[k], c->qsp,
+                             c->msp, c->cloud_start, c->n_clouds, c->en_out, c->s);
+        std::vector<double> per(6 * (size_t)c->n_clouds);
+        CK(cudaMemcpyAsync(per.data(), c->en_out, sizeof(double) * per.size(),
+                           cudaMemcpyDeviceToHost, c->s));
+        CK(cudaStreamSynchronize(c->s));
+        c->cloud_energy = per;
+        for (int cl = 0; cl < c->n_clouds; ++cl)
+            for (int j = 0; j < 6; ++j) r[j] += per[6 * cl + j];
+    }
     if ((rc = check_launch(c, "energy"))) return rc;
     if ((rc = device_error(c))) return rc;
     out[0] = r[0];
@@ -595,6 +720,49 @@ int ucp_energy(ucp_ctx* c, double theta, double eps, double out[6])
     out[3] = r[0] + r[1] + r[2];
     out[4] = std::sqrt(r[3] * r[3] + r[4] * r[4] + r[5] * r[5]);
     out[5] = (double)c->steps;
+    return UCP_OK;
+}
+
+int ucp_energy_clouds(ucp_ctx* c, double theta, double eps, double* out)
+{
+    if (!c || !out) return UCP_EINVAL;
+    double tot[6];
+    int rc = ucp_energy(c, theta, eps, tot);
+    if (rc) return rc;
+    for (int cl = 0; cl < c->n_clouds; ++cl) {
+        const double* r = c->n_clouds == 1 ? nullptr : &c->cloud_energy[6 * cl];
+        double v[6];
+        if (r) {
+            for (int j = 0; j < 6; ++j) v[j] = r[j];
+        }
+        double* o = out + 6 * (size_t)cl;
+        if (!r) {
+            for (int j = 0; j < 6; ++j) o[j] = tot[j];
+            continue;
+        }
+        o[0] = v[0];
+        o[1] = v[1];
+        o[2] = v[2];
+        o[3] = v[0] + v[1] + v[2];
+        o[4] = std::sqrt(v[3] * v[3] + v[4] * v[4] + v[5] * v[5]);
+        o[5] = (double)c->steps;
+    }
+    return UCP_OK;
+}
+
+int ucp_get_cubes(ucp_ctx* c, double* out)
+{
+    if (!c || !out) return UCP_EINVAL;
+    if (!c->tree_valid) return fail(c, UCP_ESTATE, "no tree built");
+    std::vector<Cube> cb(c->n_clouds);
+    CK(cudaMemcpyAsync(cb.data(), c->cube, sizeof(Cube) * cb.size(), cudaMemcpyDeviceToHost, c->s));
+    CK(cudaStreamSynchronize(c->s));
+    for (int cl = 0; cl < c->n_clouds; ++cl) {
+        out[4 * cl] = cb[cl].c[0];
+        out[4 * cl + 1] = cb[cl].c[1];
+        out[4 * cl + 2] = cb[cl].c[2];
+        out[4 * cl + 3] = cb[cl].L;
+    }
     return UCP_OK;
 }
 
@@ -649,7 +817,7 @@ int ucp_get_sorted(ucp_ctx* c, uint64_t* keys, uint32_t* ids, int on_device)
     if (!c->tree_valid) return fail(c, UCP_ESTATE, "no tree built");
     size_t n = (size_t)c->n;
     cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
-    if (keys) CK(cudaMemcpyAsync(keys, c->key[0], n * 8, kind, c->s));
+    if (keys) CK(cudaMemcpyAsync(keys, c->key[c->sorted_buf], n * 8, kind, c->s));
     if (ids) CK(cudaMemcpyAsync(ids, c->id[c->cur], n * 4, kind, c->s));
     if (!on_device) CK(cudaStreamSynchronize(c->s));
     return UCP_OK;
@@ -668,9 +836,10 @@ int ucp_get_tree(ucp_ctx* c, int64_t* nnodes, int64_t cap, int32_t* topo, int8_t
     if (!c || !nnodes) return UCP_EINVAL;
     if (!c->tree_valid) return fail(c, UCP_ESTATE, "no tree built");
     int nn = 0;
-    Cube cb;
+    std::vector<Cube> cubes(c->n_clouds);
     CK(cudaMemcpyAsync(&nn, c->t.nnodes, sizeof(int), cudaMemcpyDeviceToHost, c->s));
-    CK(cudaMemcpyAsync(&cb, c->cube, sizeof(cb), cudaMemcpyDeviceToHost, c->s));
+    CK(cudaMemcpyAsync(cubes.data(), c->cube, sizeof(Cube) * cubes.size(), cudaMemcpyDeviceToHost,
+                       c->s));
     CK(cudaStreamSynchronize(c->s));
     *nnodes = nn;
     if (!topo && !is_leaf && !geom) return UCP_OK;
@@ -695,6 +864,9 @@ int ucp_get_tree(ucp_ctx* c, int64_t* nnodes, int64_t cap, int32_t* topo, int8_t
         }
         if (is_leaf) is_leaf[i] = (dl[i] & 256) ? 1 : 0;
         if (geom) {
+            const int cl = (int)(std::upper_bound(c->cloud_start_h.begin(), c->cloud_start_h.end(),
+                                                  info[i].x) - c->cloud_start_h.begin()) - 1;
+            const Cube& cb = cubes[cl];
             double* g = geom + 20 * (size_t)i;
             double s = std::ldexp(cb.L, -d);
             unsigned int ic[3] = {host_compact3(cell[i]), host_compact3(cell[i] >> 1),

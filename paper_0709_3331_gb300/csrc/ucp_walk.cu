@@ -114,7 +114,6 @@ k_walk_fp64(WalkArgs a)
     __shared__ WarpList L[kWalkWarps];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     WarpList& lst = L[w];
-    const int nn = *a.t.nnodes;
     const double q0 = a.qsp[0], q1 = a.qsp[1];
     const double* __restrict__ mom = a.t.mom;
     const int4* __restrict__ info = a.t.info;
@@ -124,11 +123,15 @@ k_walk_fp64(WalkArgs a)
     const double* __restrict__ Z = a.z;
     const int8_t* __restrict__ SP = a.sp;
 
-    for (int chunk = next_chunk(a.work, lane); chunk * 32 < a.ntargets;
+    for (int chunk = next_chunk(a.work, lane); chunk < a.nchunks;
          chunk = next_chunk(a.work, lane)) {
-        const int ti = chunk * 32 + lane;
-        const bool valid = ti < a.ntargets;
+        // up to 32 key-consecutive targets of one cloud, walked through that cloud's tree
+        const int4 ck = a.chunks[chunk];
+        const int ti = ck.x + lane;
+        const bool valid = lane < ck.y;
         const int t = valid ? (a.targets ? a.targets[ti] : ti) : -1;
+        const int root = a.pos_off[a.t.cloud_start ? a.t.cloud_start[ck.z] : 0];
+        const int end = info[root].z;
         const double xt = valid ? X[t] : 0.0, yt = valid ? Y[t] : 0.0, zt = valid ? Z[t] : 0.0;
         const int8_t st = valid ? SP[t] : 0;
         double ex = 0.0, ey = 0.0, ez = 0.0, ph = 0.0;
@@ -179,8 +182,8 @@ k_walk_fp64(WalkArgs a)
             __syncwarp();
         };
 
-        int node = 0;
-        while (node < nn) {
+        int node = root;
+        while (node < end) {
             const double* m = mom + (size_t)node * kMom;
             const int4 inf = info[node];
             const bool leaf = (dlf[node] & 256) != 0;
@@ -269,17 +272,20 @@ k_walk_fp32c(WalkArgs a)
     __shared__ WarpList L[kWalkWarps];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     WarpList& lst = L[w];
-    const int nn = *a.t.nnodes;
     const double q0 = a.qsp[0], q1 = a.qsp[1];
     const float4* __restrict__ F = a.t.f32;
     const float4* __restrict__ S = a.src32;
     const float eps2 = (float)a.eps2;
 
-    for (int chunk = next_chunk(a.work, lane); chunk * 32 < a.ntargets;
+    for (int chunk = next_chunk(a.work, lane); chunk < a.nchunks;
          chunk = next_chunk(a.work, lane)) {
-        const int ti = chunk * 32 + lane;
-        const bool valid = ti < a.ntargets;
+        // up to 32 key-consecutive targets of one cloud, walked through that cloud's tree
+        const int4 ck = a.chunks[chunk];
+        const int ti = ck.x + lane;
+        const bool valid = lane < ck.y;
         const int t = valid ? (a.targets ? a.targets[ti] : ti) : -1;
+        const int root = a.pos_off[a.t.cloud_start ? a.t.cloud_start[ck.z] : 0];
+        const int end = __float_as_int(F[(size_t)root * kF32 + 1].w);
         // target as an unevaluated float pair: x = xh + xl
         float xh = 0.f, yh = 0.f, zh = 0.f, xl = 0.f, yl = 0.f, zl = 0.f;
         if (valid) {
@@ -394,8 +400,8 @@ k_walk_fp32c(WalkArgs a)
             __syncwarp();
         };
 
-        int node = 0;
-        while (node < nn) {
+        int node = root;
+        while (node < end) {
             const float4* r = F + (size_t)node * kF32;
             const float4 A = r[0], B = r[1], C = r[2], D = r[3], E = r[4];
             const int nxt = __float_as_int(B.w);
@@ -473,10 +479,10 @@ k_walk_fp32c(WalkArgs a)
 __global__ void k_mac_prepare(Tree t, const Cube* __restrict__ cube, double theta, int want_f32)
 {
     const int nn = *t.nnodes;
-    const double L = cube->L;
     for (int nd = blockIdx.x * blockDim.x + threadIdx.x; nd < nn; nd += gridDim.x * blockDim.x) {
         double* m = t.mom + (size_t)nd * kMom;
         int dl = t.depth_leaf[nd];
+        const double L = cube[t.cloud ? t.cloud[t.info[nd].x] : 0].L;
         double s = ldexp(L, -(dl & 255));
         double r2;
         if (theta > 0.0) {
@@ -512,11 +518,10 @@ void launch_mac_prepare(Tree t, const Cube* cube, double theta, int want_f32, cu
     k_mac_prepare<<<blocks, 256, 0, s>>>(t, cube, theta, want_f32);
 }
 
-static int walk_blocks(int ntargets, int nsm, int per_sm)
+static int walk_blocks(int nchunks, int nsm, int per_sm)
 {
-    int chunks = (ntargets + 31) / 32;
     int blocks = nsm * per_sm;
-    int need = (chunks + kWalkWarps - 1) / kWalkWarps;
+    int need = (nchunks + kWalkWarps - 1) / kWalkWarps;
     if (blocks > need) blocks = need;
     return blocks < 1 ? 1 : blocks;
 }
@@ -525,16 +530,16 @@ void launch_walk_fp64(const WalkArgs& a, int nsm, cudaStream_t s)
 {
     count_launch(1);
     cudaMemsetAsync(a.work, 0, sizeof(int), s);
-    if (a.kelbg) k_walk_fp64<true><<<walk_blocks(a.ntargets, nsm, 8), kWalkThreads, 0, s>>>(a);
-    else k_walk_fp64<false><<<walk_blocks(a.ntargets, nsm, 8), kWalkThreads, 0, s>>>(a);
+    if (a.kelbg) k_walk_fp64<true><<<walk_blocks(a.nchunks, nsm, 8), kWalkThreads, 0, s>>>(a);
+    else k_walk_fp64<false><<<walk_blocks(a.nchunks, nsm, 8), kWalkThreads, 0, s>>>(a);
 }
 
 void launch_walk_fp32c(const WalkArgs& a, int nsm, cudaStream_t s)
 {
     count_launch(1);
     cudaMemsetAsync(a.work, 0, sizeof(int), s);
-    if (a.kelbg) k_walk_fp32c<true><<<walk_blocks(a.ntargets, nsm, 12), kWalkThreads, 0, s>>>(a);
-    else k_walk_fp32c<false><<<walk_blocks(a.ntargets, nsm, 12), kWalkThreads, 0, s>>>(a);
+    if (a.kelbg) k_walk_fp32c<true><<<walk_blocks(a.nchunks, nsm, 12), kWalkThreads, 0, s>>>(a);
+    else k_walk_fp32c<false><<<walk_blocks(a.nchunks, nsm, 12), kWalkThreads, 0, s>>>(a);
 }
 
 }  // namespace ucp

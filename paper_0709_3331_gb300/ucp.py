@@ -24,7 +24,8 @@ UCP_POT_PLUMMER, UCP_POT_KELBG = 0, 1
 EXPORTS = ("ucp_create", "ucp_destroy", "ucp_set_state", "ucp_get_state", "ucp_tree_build",
            "ucp_tree_force", "ucp_step", "ucp_energy", "ucp_stats", "ucp_get_cube",
            "ucp_get_sorted", "ucp_get_tree", "ucp_get_counts", "ucp_profile", "ucp_profile_read",
-           "ucp_strerror", "ucp_last_error", "ucp_selftest_wait_timeout")
+           "ucp_strerror", "ucp_last_error", "ucp_selftest_wait_timeout", "ucp_create_batch",
+           "ucp_energy_clouds", "ucp_get_cubes")
 
 
 class UcpError(RuntimeError):
@@ -66,6 +67,12 @@ def lib():
         L.ucp_get_counts.argtypes = [vp, vp, vp, i32]
         L.ucp_profile.argtypes = [vp, i32]
         L.ucp_profile_read.argtypes = [vp, C.POINTER(dbl), C.POINTER(i64)]
+        L.ucp_create_batch.argtypes = [C.POINTER(vp), C.POINTER(ucp_params), C.c_int32, vp]
+        L.ucp_create_batch.restype = C.c_int
+        L.ucp_energy_clouds.argtypes = [vp, dbl, dbl, vp]
+        L.ucp_energy_clouds.restype = C.c_int
+        L.ucp_get_cubes.argtypes = [vp, vp]
+        L.ucp_get_cubes.restype = C.c_int
         L.ucp_selftest_wait_timeout.argtypes = [vp]
         L.ucp_selftest_wait_timeout.restype = C.c_int
         L.ucp_strerror.argtypes = [i32]
@@ -105,7 +112,9 @@ class Context:
     """One particle set on the current CUDA device (``ucp_create`` .. ``ucp_destroy``)."""
 
     def __init__(self, n, q=(1.0, -1.0), m=(1000.0, 1.0), leaf_cap=16, precision=UCP_FP64,
-                 stream=None, kelbg_lambda=None):
+                 stream=None, kelbg_lambda=None, sizes=None):
+        """``sizes``: particle counts of an ensemble of independent clouds
+        (``ucp_create_batch``); their total must equal ``n``."""
         L = lib()
         p = ucp_params()
         p.n = int(n)
@@ -126,7 +135,13 @@ class Context:
             p.lambda_ei = float(kelbg_lambda)
         self.n = int(n)
         self._h = C.c_void_p()
-        rc = L.ucp_create(C.byref(self._h), C.byref(p))
+        if sizes is None:
+            self.n_clouds = 1
+            rc = L.ucp_create(C.byref(self._h), C.byref(p))
+        else:
+            sz = np.ascontiguousarray(sizes, dtype=np.int64)
+            self.n_clouds = int(sz.shape[0])
+            rc = L.ucp_create_batch(C.byref(self._h), C.byref(p), self.n_clouds, sz.ctypes.data)
         if rc:
             raise UcpError(rc, "ucp_create: " + L.ucp_strerror(rc).decode())
 
@@ -191,6 +206,17 @@ class Context:
         out = np.zeros(6)
         self._check(lib().ucp_energy(self._h, float(theta), float(eps), out.ctypes.data),
                     "ucp_energy")
+        return out
+
+    def energy_clouds(self, theta, eps):
+        out = np.zeros((self.n_clouds, 6))
+        self._check(lib().ucp_energy_clouds(self._h, float(theta), float(eps), out.ctypes.data),
+                    "ucp_energy_clouds")
+        return out
+
+    def get_cubes(self):
+        out = np.zeros((self.n_clouds, 4))
+        self._check(lib().ucp_get_cubes(self._h, out.ctypes.data), "ucp_get_cubes")
         return out
 
     def stats(self, reset=False):
