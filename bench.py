@@ -439,6 +439,48 @@ def run_extras(c, W, ws, pos_d, vel_d, sp_d, Context, UCP_FP32C, UCP_FP64, timed
                           "walk_frac_fp32_peak": fl / (wm / 1e3) / 1e12 / peak}
         cs.close()
     extra["theta_sweep"] = sweep
+
+    # ensemble of 64 independent clouds (sizes log-uniform 4096..65536, sigma_c =
+    # (N_c/2048)^(1/3)) in one context: every stage one launch for all clouds
+    from paper_0709_3331_gb300.inputs import batched_sizes, gaussian_cloud
+    ns, _ = batched_sizes()
+    cl = [gaussian_cloud(n, (n / 2048.0) ** (1.0 / 3.0), 4000 + i) for i, n in enumerate(ns)]
+    bpos = torch.from_numpy(np.concatenate([x.pos for x in cl])).cuda()
+    bvel = torch.from_numpy(np.concatenate([x.vel for x in cl])).cuda()
+    bsp = torch.from_numpy(np.concatenate([x.species for x in cl])).cuda()
+    ntot = int(sum(ns))
+    cb = Context(ntot, c.q, c.m, leaf_cap=W["leaf_cap"], precision=UCP_FP32C, sizes=ns)
+    cb.set_state(bpos, bvel, bsp)
+    cb.step(W["dt_e"], W["k"], W["k"], 0.5, W["eps"])
+    torch.cuda.synchronize()
+    msb, stb, wmb, wnb, _ = timed_steps(cb, 2)
+    extra["batched_64_clouds"] = {
+        "n_total": ntot, "clouds": len(ns), "ms_per_step": msb / 2,
+        "interactions_per_s": float(stb[0] + stb[1]) / (msb / 1e3),
+        "particle_steps_per_s": ntot * W["k"] * 2 / (msb / 1e3),
+        "walk_frac_fp32_peak": (FLOP_P2P * float(stb[0]) + FLOP_M2P * float(stb[1]))
+        / (wmb / 1e3) / 1e12 / peak,
+        "step": "one block of 10 electron substeps for all 64 clouds, theta 0.5, FP32C"}
+    cb.close()
+
+    # plain method in FP64: N = 131072, sigma 4, 100 electron substeps (10 blocks)
+    c1 = gaussian_cloud(131072, 4.0, 2)
+    cp = Context(c1.n, c1.q, c1.m, leaf_cap=W["leaf_cap"], precision=UCP_FP64)
+    cp.set_state(c1.pos, c1.vel, c1.species)
+    e0 = cp.energy(0.5, W["eps"])
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    cp.step(W["dt_e"], W["k"], 100, 0.5, W["eps"])
+    t1.record(stream)
+    torch.cuda.synchronize()
+    mp = t0.elapsed_time(t1)
+    e1 = cp.energy(0.5, W["eps"])
+    extra["plain_fp64_n131072"] = {
+        "electron_steps": 100, "ms": mp, "particle_steps_per_s": c1.n * 100 / (mp / 1e3),
+        "energy_drift": abs(e1[3] - e0[3]) / (e0[0] + e0[1] + abs(e0[2]))}
+    cp.close()
     return extra
 
 

@@ -84,6 +84,13 @@ def lib():
                                      C.c_int, C.c_int, _d, C.c_int]
             L.orc_has_openmp.restype = C.c_int
             L.orc_set_potential.argtypes = [C.c_int, C.c_double]
+            L.orc_tree_force_adjoint.argtypes = [C.c_void_p, _d, _i8, _d, _d, C.c_double,
+                                                 C.c_double, _d, _d]
+            L.orc_direct_force_adjoint.argtypes = [C.c_int64, _d, _i8, _d, _d, C.c_double, _d, _d]
+            L.orc_run_adjoint_ke_e.argtypes = [C.c_int64, _d, _d, _i8, _d, _d, C.c_double, C.c_int,
+                                               C.c_int64, C.c_double, C.c_double, C.c_int, C.c_int,
+                                               _d, _d, C.c_int]
+            L.orc_run_adjoint_ke_e.restype = C.c_double
             L.orc_cluster_multipole.argtypes = [C.c_int64, _d, _i8, _d, C.c_double, _d, C.c_int,
                                                 _d, _d]
             _lib = L
@@ -243,6 +250,31 @@ def cluster_multipole(pos, species, q, eps, xt, term_mask=7):
     lib().orc_cluster_multipole(pos.shape[0], pos, species, q, float(eps),
                                 np.ascontiguousarray(xt, dtype=np.float64), int(term_mask), E, phi)
     return E, float(phi[0])
+
+
+def force_adjoint(pos, species, q, m, lam, theta, eps, leaf_cap=1, direct_sum=False):
+    """mu = (d a / d x)^T lam for a = q E / m (tree held fixed, or the direct sum)."""
+    pos, species, q, m = _pos(pos), _sp(species), _qm(q), _qm(m)
+    lam = _pos(lam)
+    mu = np.zeros_like(pos)
+    if direct_sum:
+        lib().orc_direct_force_adjoint(pos.shape[0], pos, species, q, m, float(eps), lam, mu)
+    else:
+        T = Tree(pos, species, q, leaf_cap)
+        lib().orc_tree_force_adjoint(T._h, pos, species, q, m, float(theta), float(eps), lam, mu)
+    return mu
+
+
+def run_adjoint_ke_e(pos, vel, species, q, m, dt_e, k, nblocks, theta, eps, leaf_cap=1,
+                     direct_sum=False, nthreads=1):
+    """(L, dL/dx0, dL/dv0) for L = electron kinetic energy after ``nblocks`` blocks."""
+    pos, vel = _pos(pos), _pos(vel)
+    gx = np.zeros_like(pos)
+    gv = np.zeros_like(pos)
+    L = lib().orc_run_adjoint_ke_e(pos.shape[0], pos, vel, _sp(species), _qm(q), _qm(m),
+                                   float(dt_e), int(k), int(nblocks), float(theta), float(eps),
+                                   int(leaf_cap), int(bool(direct_sum)), gx, gv, int(nthreads))
+    return L, gx, gv
 
 
 def accel(pos, species, q, m, theta, eps, leaf_cap=1, direct_sum=False, nthreads=1):

@@ -673,3 +673,284 @@ void orc_cluster_multipole(int64_t n, const double* pos, const int8_t* species,
     if (T->nnodes > 0) multipole_field(T, 0, xt, eps * eps, term_mask, E, phi);
     orc_tree_free(T);
 }
+
+/* ------------------------------------------------------------------ */
+/* Adjoint of the TREE force (the derivative the split-step push needs to carry
+ * gradients back through a run).  For a cotangent lambda (n x 3, per original
+ * index) it returns mu = (d a / d x)^T lambda, a = q E / m, with the tree held
+ * fixed (which boxes each target opens or accepts does not move under an
+ * infinitesimal displacement).  Every piece is the exact derivative of what
+ * orc_tree_force computes:
+ *   - a direct pair: J(r) = d/dr [r g^3] = g^3 I - 3 g^5 r r^T, on the target
+ *     side and, with the opposite sign, on the source side;
+ *   - an accepted box, target side: the field gradient of the expansion,
+ *     -(M grad grad g - D . grad^3 g + 1/2 Q : grad^4 g);
+ *   - an accepted box, source side: through D and Q at fixed centre
+ *     (q_s [alpha - Gamma y_s]) and through the centre c = sum |q| x / S0 that
+ *     the expansion is taken about (|q_s| / S0 kappa), where, with
+ *     w = q_t lambda_t / m_t summed over the targets that accept the box,
+ *     alpha = grad grad g w, Gamma_ec = w_a d_aec g, kappa = 1/2 grad^4 g[w, ., Q].
+ * Derivatives of g = (R.R + eps^2)^(-1/2):
+ *   d_ab g   = 3 R_a R_b g^5 - d_ab g^3
+ *   d_abc g  = -15 R_a R_b R_c g^7 + 3 (d_ab R_c + d_ac R_b + d_bc R_a) g^5
+ *   d_abcd g = 105 R_a R_b R_c R_d g^9 - 15 (six d_xy R R terms) g^7
+ *              + 3 (d_ab d_cd + d_ac d_bd + d_ad d_bc) g^5 */
+static double dot3(const double* a, const double* b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+
+/* Q (xx xy xz yy yz zz) times v */
+static void qmul(const double* Q, const double* v, double out[3])
+{
+    out[0] = Q[0] * v[0] + Q[1] * v[1] + Q[2] * v[2];
+    out[1] = Q[1] * v[0] + Q[3] * v[1] + Q[4] * v[2];
+    out[2] = Q[2] * v[0] + Q[4] * v[1] + Q[5] * v[2];
+}
+
+/* sum_bcd v_b Q_cd d_abcd g, free index a */
+static void t4(const double R[3], const double v[3], const double* Q, double g, double out[3])
+{
+    double g2 = g * g, g5 = g2 * g2 * g, g7 = g5 * g2, g9 = g7 * g2;
+    double QR[3], Qv[3];
+    qmul(Q, R, QR);
+    qmul(Q, v, Qv);
+    double RQR = dot3(R, QR), Rv = dot3(R, v), vQR = dot3(v, QR), trQ = Q[0] + Q[3] + Q[5];
+    for (int a = 0; a < 3; ++a)
+        out[a] = 105.0 * R[a] * Rv * RQR * g9
+                 - 15.0 * g7 * (v[a] * RQR + 2.0 * Rv * QR[a] + 2.0 * R[a] * vQR + R[a] * Rv * trQ)
+                 + 3.0 * g5 * (v[a] * trQ + 2.0 * Qv[a]);
+}
+
+typedef struct {
+    const orc_tree* T;
+    const double* pos;
+    const int8_t* species;
+    const double *q, *m;
+    double theta, eps2;
+    double *alpha, *gam, *kap, *mu;
+} adj_args;
+
+static void walk_adj(const adj_args* A, int64_t nd, int64_t t, const double xt[3], const double lam[3],
+                     const double w[3], double qt_over_mt, double mu_t[3])
+{
+    const orc_tree* T = A->T;
+    if (A->theta > 0.0) {
+        double rcrit = T->side[nd] / A->theta + T->delta[nd];
+        double dx = xt[0] - T->c[3 * nd];
+        double dy = xt[1] - T->c[3 * nd + 1];
+        double dz = xt[2] - T->c[3 * nd + 2];
+        double d2 = dx * dx + dy * dy + dz * dz;
+        if (rcrit * rcrit < d2) {
+            const double* D = &T->D[3 * nd];
+            const double* Q = &T->Q[6 * nd];
+            double M = T->M[nd];
+            double R[3] = {dx, dy, dz};
+            double g = 1.0 / sqrt(d2 + A->eps2);
+            double g2 = g * g, g3 = g2 * g, g5 = g3 * g2, g7 = g5 * g2;
+            /* target side: -(M grad grad g lam - sum_bc lam_b D_c d_abc g + 1/2 T4(lam)) */
+            double Rl = dot3(R, lam), RD = dot3(R, D), lD = dot3(lam, D);
+            double T4l[3];
+            t4(R, lam, Q, g, T4l);
+            for (int a = 0; a < 3; ++a) {
+                double hess = M * (3.0 * R[a] * Rl * g5 - lam[a] * g3);
+                double dterm = -15.0 * R[a] * Rl * RD * g7 + 3.0 * (lam[a] * RD + D[a] * Rl + R[a] * lD) * g5;
+                mu_t[a] += qt_over_mt * -(hess - dterm + 0.5 * T4l[a]);
+            }
+            /* source side accumulators of the box */
+            double Rw = dot3(R, w);
+            double T4w[3];
+            t4(R, w, Q, g, T4w);
+            for (int a = 0; a < 3; ++a) {
+                A->alpha[3 * nd + a] += 3.0 * R[a] * Rw * g5 - w[a] * g3;
+                A->kap[3 * nd + a] += 0.5 * T4w[a];
+            }
+            const int ia[6] = {0, 0, 0, 1, 1, 2}, ib[6] = {0, 1, 2, 1, 2, 2};
+            for (int k = 0; k < 6; ++k) {
+                int e = ia[k], c = ib[k];
+                A->gam[6 * nd + k] += -15.0 * Rw * R[e] * R[c] * g7 +
+                                      3.0 * (w[e] * R[c] + w[c] * R[e] + (e == c ? Rw : 0.0)) * g5;
+            }
+            return;
+        }
+    }
+    if (T->is_leaf[nd]) {
+        for (int64_t sl = T->begin[nd]; sl < T->end[nd]; ++sl) {
+            int64_t j = T->slot[sl];
+            if (j == t) continue;
+            double qj = A->q[A->species[j]];
+            double r[3] = {xt[0] - A->pos[3 * j], xt[1] - A->pos[3 * j + 1], xt[2] - A->pos[3 * j + 2]};
+            double g = 1.0 / sqrt(dot3(r, r) + A->eps2);
+            double g3 = g * g * g, g5 = g3 * g * g;
+            double rl = dot3(r, lam), rw = dot3(r, w);
+            for (int a = 0; a < 3; ++a) {
+                mu_t[a] += qt_over_mt * qj * (lam[a] * g3 - 3.0 * r[a] * rl * g5);
+                A->mu[3 * j + a] -= qj * (w[a] * g3 - 3.0 * r[a] * rw * g5);
+            }
+        }
+        return;
+    }
+    for (int64_t ch = nd + 1; ch < T->next[nd]; ch = T->next[ch])
+        walk_adj(A, ch, t, xt, lam, w, qt_over_mt, mu_t);
+}
+
+void orc_tree_force_adjoint(const orc_tree* T, const double* pos, const int8_t* species,
+                            const double q[2], const double m[2], double theta, double eps,
+                            const double* lam, double* mu)
+{
+    int64_t n = T->n, nn = T->nnodes;
+    adj_args A;
+    A.T = T;
+    A.pos = pos;
+    A.species = species;
+    A.q = q;
+    A.m = m;
+    A.theta = theta;
+    A.eps2 = eps * eps;
+    A.alpha = (double*)calloc((size_t)(3 * nn + 1), sizeof(double));
+    A.gam = (double*)calloc((size_t)(6 * nn + 1), sizeof(double));
+    A.kap = (double*)calloc((size_t)(3 * nn + 1), sizeof(double));
+    A.mu = mu;
+    memset(mu, 0, sizeof(double) * 3 * (size_t)n);
+    for (int64_t t = 0; t < n; ++t) {
+        const double* l = &lam[3 * t];
+        if (l[0] == 0.0 && l[1] == 0.0 && l[2] == 0.0) continue;
+        double qm = q[species[t]] / m[species[t]];
+        double w[3] = {qm * l[0], qm * l[1], qm * l[2]};
+        double mu_t[3] = {0.0, 0.0, 0.0};
+        if (nn > 0) walk_adj(&A, 0, t, &pos[3 * t], l, w, qm, mu_t);
+        for (int a = 0; a < 3; ++a) mu[3 * t + a] += mu_t[a];
+    }
+    /* push the box accumulators down to the particles of each box */
+    for (int64_t nd = 0; nd < nn; ++nd) {
+        const double* c = &T->c[3 * nd];
+        const double* G = &A.gam[6 * nd];
+        for (int64_t sl = T->begin[nd]; sl < T->end[nd]; ++sl) {
+            int64_t s = T->slot[sl];
+            double qs = q[species[s]];
+            double y[3] = {pos[3 * s] - c[0], pos[3 * s + 1] - c[1], pos[3 * s + 2] - c[2]};
+            double Gy[3];
+            qmul(G, y, Gy);
+            double cw = T->S0[nd] > 0.0 ? fabs(qs) / T->S0[nd] : 0.0;
+            for (int a = 0; a < 3; ++a)
+                mu[3 * s + a] += qs * (A.alpha[3 * nd + a] - Gy[a]) + cw * A.kap[3 * nd + a];
+        }
+    }
+    free(A.alpha);
+    free(A.gam);
+    free(A.kap);
+}
+
+/* Adjoint of the direct sum (the same pair derivative over all pairs). */
+void orc_direct_force_adjoint(int64_t n, const double* pos, const int8_t* species, const double q[2],
+                              const double m[2], double eps, const double* lam, double* mu)
+{
+    double eps2 = eps * eps;
+    memset(mu, 0, sizeof(double) * 3 * (size_t)n);
+    for (int64_t t = 0; t < n; ++t) {
+        const double* l = &lam[3 * t];
+        double qm = q[species[t]] / m[species[t]];
+        double w[3] = {qm * l[0], qm * l[1], qm * l[2]};
+        for (int64_t j = 0; j < n; ++j) {
+            if (j == t) continue;
+            double qj = q[species[j]];
+            double r[3] = {pos[3 * t] - pos[3 * j], pos[3 * t + 1] - pos[3 * j + 1], pos[3 * t + 2] - pos[3 * j + 2]};
+            double g = 1.0 / sqrt(dot3(r, r) + eps2);
+            double g3 = g * g * g, g5 = g3 * g * g;
+            double rl = dot3(r, l), rw = dot3(r, w);
+            for (int a = 0; a < 3; ++a) {
+                mu[3 * t + a] += qm * qj * (l[a] * g3 - 3.0 * r[a] * rl * g5);
+                mu[3 * j + a] -= qj * (w[a] * g3 - 3.0 * r[a] * rw * g5);
+            }
+        }
+    }
+}
+
+static void force_adjoint_at(int64_t n, const double* x, const int8_t* species, const double q[2],
+                             const double m[2], double theta, double eps, int leaf_cap,
+                             int use_direct, const double* lam, double* mu)
+{
+    if (use_direct) {
+        orc_direct_force_adjoint(n, x, species, q, m, eps, lam, mu);
+    } else {
+        orc_tree* T = orc_tree_build(n, x, species, q, leaf_cap);
+        orc_tree_force_adjoint(T, x, species, q, m, theta, eps, lam, mu);
+        orc_tree_free(T);
+    }
+}
+
+/* Gradient of L = electron kinetic energy after nblocks blocks of orc_run (from
+ * (pos, vel) with no stored accelerations) with respect to the initial
+ * positions and velocities: the push run forward once, every substep position
+ * kept, then the exact reverse of each kick and drift (velocity Verlet is
+ * linear in v, and each kick v += h a(x) sends lambda_x += h (da/dx)^T lambda_v
+ * on the kicked species' rows).  Returns L. */
+double orc_run_adjoint_ke_e(int64_t n, const double* pos, const double* vel, const int8_t* species,
+                            const double q[2], const double m[2], double dt_e, int k,
+                            int64_t nblocks, double theta, double eps, int leaf_cap, int use_direct,
+                            double* grad_x, double* grad_v, int nthreads)
+{
+    int64_t S = nblocks * k;
+    size_t nb3 = 3 * (size_t)n;
+    double* X = (double*)malloc(sizeof(double) * nb3 * (size_t)(S + 1));
+    double* v = (double*)malloc(sizeof(double) * nb3);
+    double* acc = (double*)malloc(sizeof(double) * nb3);
+    memcpy(X, pos, sizeof(double) * nb3);
+    memcpy(v, vel, sizeof(double) * nb3);
+    accel(n, X, species, q, m, theta, eps, leaf_cap, use_direct, 0, acc, nthreads);
+    double dt_i = k * dt_e;
+    for (int64_t b = 0; b < nblocks; ++b) {
+        for (int64_t i = 0; i < n; ++i)
+            if (species[i] == 0)
+                for (int c = 0; c < 3; ++c) v[3 * i + c] += 0.5 * dt_i * acc[3 * i + c];
+        for (int s = 1; s <= k; ++s) {
+            int64_t g = b * k + s;
+            double* xp = X + nb3 * (size_t)(g - 1);
+            double* xg = X + nb3 * (size_t)g;
+            for (int64_t i = 0; i < n; ++i)
+                if (species[i] == 1)
+                    for (int c = 0; c < 3; ++c) v[3 * i + c] += 0.5 * dt_e * acc[3 * i + c];
+            for (size_t i = 0; i < nb3; ++i) xg[i] = xp[i] + dt_e * v[i];
+            accel(n, xg, species, q, m, theta, eps, leaf_cap, use_direct, s < k, acc, nthreads);
+            for (int64_t i = 0; i < n; ++i)
+                if (species[i] == 1)
+                    for (int c = 0; c < 3; ++c) v[3 * i + c] += 0.5 * dt_e * acc[3 * i + c];
+        }
+        for (int64_t i = 0; i < n; ++i)
+            if (species[i] == 0)
+                for (int c = 0; c < 3; ++c) v[3 * i + c] += 0.5 * dt_i * acc[3 * i + c];
+    }
+    double L = 0.0;
+    double* lx = grad_x;
+    double* lv = grad_v;
+    for (int64_t i = 0; i < n; ++i)
+        for (int c = 0; c < 3; ++c) {
+            lx[3 * i + c] = 0.0;
+            lv[3 * i + c] = species[i] == 1 ? m[1] * v[3 * i + c] : 0.0;
+            if (species[i] == 1) L += 0.5 * m[1] * v[3 * i + c] * v[3 * i + c];
+        }
+    double* lam = (double*)malloc(sizeof(double) * nb3);
+    double* mu = (double*)malloc(sizeof(double) * nb3);
+#define KICK_ADJ(XPOS, H, SPEC)                                                                \
+    do {                                                                                       \
+        for (int64_t i = 0; i < n; ++i)                                                        \
+            for (int c = 0; c < 3; ++c)                                                        \
+                lam[3 * i + c] = species[i] == (SPEC) ? (H) * lv[3 * i + c] : 0.0;             \
+        force_adjoint_at(n, XPOS, species, q, m, theta, eps, leaf_cap, use_direct, lam, mu);   \
+        for (size_t i = 0; i < nb3; ++i) lx[i] += mu[i];                                       \
+    } while (0)
+    for (int64_t b = nblocks - 1; b >= 0; --b) {
+        KICK_ADJ(X + nb3 * (size_t)((b + 1) * k), 0.5 * dt_i, 0);
+        for (int s = k; s >= 1; --s) {
+            int64_t g = b * k + s;
+            KICK_ADJ(X + nb3 * (size_t)g, 0.5 * dt_e, 1);
+            for (size_t i = 0; i < nb3; ++i) lv[i] += dt_e * lx[i];
+            KICK_ADJ(X + nb3 * (size_t)(g - 1), 0.5 * dt_e, 1);
+        }
+        KICK_ADJ(X + nb3 * (size_t)(b * k), 0.5 * dt_i, 0);
+    }
+#undef KICK_ADJ
+    free(lam);
+    free(mu);
+    free(X);
+    free(v);
+    free(acc);
+    return L;
+}
