@@ -124,6 +124,23 @@ int ucp_tree_force(ucp_ctx* ctx, double theta, double eps, double* acc, double* 
 int ucp_step(ucp_ctx* ctx, double dt_e, int ion_substep_ratio, int64_t n_electron_steps,
              double theta, double eps);
 
+/* Gradient of the electron kinetic energy after a run.  From the current state
+ * (x0, v0), advances n_steps electron substeps exactly as ucp_step(dt_e, k,
+ * n_steps, theta, eps) and returns *loss = L = sum over electrons of m v^2 / 2 at
+ * the end, grad_x = dL/dx0 and grad_v = dL/dv0 (N x 3, caller order; either may
+ * be NULL).  Reverse mode: the discrete adjoint of every kick and drift, and at
+ * every substep the adjoint of the TREE force with the tree held fixed (the same
+ * boxes as the forward walk), evaluated in FP64; the state is kept every
+ * checkpoint_every substeps (a multiple of k) and each stretch is recomputed
+ * forward before it is reversed.  The context ends in the state after the run.
+ * This call allocates its working memory (about (n_steps / checkpoint_every +
+ * checkpoint_every) x 48 N bytes plus 96 bytes per box) and frees it before it
+ * returns.  Plummer law only (UCP_EINVAL for Kelbg contexts).  Source-side
+ * sums use atomic adds: gradients may differ between runs in the last bits. */
+int ucp_grad_ke_electrons(ucp_ctx* ctx, double dt_e, int ion_substep_ratio, int64_t n_steps,
+                          double theta, double eps, int64_t checkpoint_every, double* loss,
+                          double* grad_x, double* grad_v, int on_device);
+
 /* Sec. 5 observables of the current state: out = {KE_ion, KE_electron, PE,
  * E = KE + PE, |P| (total momentum), electron steps taken}.  PE is
  * (1/2) sum_t q_t phi_t with the tree potential; the walk over all particles

@@ -116,6 +116,18 @@ void launch_mac_prepare(Tree t, const Cube* cube, double theta, int want_f32, cu
 void launch_walk_fp64(const WalkArgs& a, int nsm, cudaStream_t s);
 void launch_walk_fp32c(const WalkArgs& a, int nsm, cudaStream_t s);
 
+// ---- adjoint (ucp_adjoint.cu) ----
+void launch_walk_adjoint(const WalkArgs& a, const double* lam, double* mu, double* adj, int nn_cap,
+                         int nsm, cudaStream_t s);
+void launch_gather3(const double* src, const unsigned int* id, int n, double* dst, cudaStream_t s);
+void launch_scatter_add3(const double* src, const unsigned int* id, int n, double* dst,
+                         cudaStream_t s);
+void launch_kick_lambda(const double* lam_v, const int8_t* sp, int n, double ce, double ci,
+                        double* out, cudaStream_t s);
+void launch_axpy3(double* y, const double* x, double a, int n, cudaStream_t s);
+void launch_ke_seed(const double* v, const int8_t* sp, int n, double me, double* lam_v,
+                    double* loss, cudaStream_t s);
+
 // ---- push and reductions (ucp_push.cu) ----
 void launch_permute(const unsigned int* perm, int n, const double* const* src6, double* const* dst6,
                     const int8_t* sp_in, int8_t* sp_out, const unsigned int* id_in,

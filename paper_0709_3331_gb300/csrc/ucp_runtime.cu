@@ -61,6 +61,7 @@ struct ucp_ctx {
     int* flags = nullptr;
     double* stage = nullptr;  // n x 6 doubles for host transfers and layout changes
     int8_t* stage_sp = nullptr;
+    int8_t* sp_caller = nullptr;  // species in caller order
     int* stage_int = nullptr;
 
     int n_e = 0;
@@ -492,6 +493,7 @@ int ucp_create_batch(ucp_ctx** out, const ucp_params* p, int32_t n_clouds, const
         (rc = dalloc(c, &c->flags, 2)))
         return bail(rc);
     if ((rc = dalloc(c, &c->stage, 6 * n)) || (rc = dalloc(c, &c->stage_sp, n)) ||
+        (rc = dalloc(c, &c->sp_caller, n)) ||
         (rc = dalloc(c, &c->stage_int, 2 * n)))
         return bail(rc);
     if (cudaMemcpyAsync(c->qsp, c->q, 2 * sizeof(double), cudaMemcpyHostToDevice, c->s) ||
@@ -561,6 +563,7 @@ int ucp_set_state(ucp_ctx* c, const double* pos, const double* vel, const int8_t
     launch_deinterleave(dpos, c->n, c->st[k][0], c->st[k][1], c->st[k][2], c->s);
     launch_deinterleave(dvel, c->n, c->st[k][3], c->st[k][4], c->st[k][5], c->s);
     launch_iota(c->id[k], c->n, c->s);
+    CK(cudaMemcpyAsync(c->sp_caller, c->sp[k], n, cudaMemcpyDeviceToDevice, c->s));
     CK(cudaMemsetAsync(c->sort.err, 0, sizeof(int), c->s));
     c->have_state = true;
     c->tree_valid = false;
@@ -636,23 +639,18 @@ int ucp_tree_force(ucp_ctx* c, double theta, double eps, double* acc, double* ph
     return UCP_OK;
 }
 
-int ucp_step(ucp_ctx* c, double dt_e, int kk, int64_t n_electron_steps, double theta, double eps)
+// The split-step push; with store != NULL the positions after every electron
+// substep are written there in caller order (n x 3 doubles per substep).
+static int run_blocks(ucp_ctx* c, double dt_e, int kk, int64_t nblocks, double theta, double eps,
+                      double* store)
 {
-    if (!c) return UCP_EINVAL;
-    if (!c->have_state) return fail(c, UCP_ESTATE, "no state");
-    if (!(dt_e > 0.0) || !std::isfinite(dt_e)) return fail(c, UCP_EINVAL, "dt_e must be > 0");
-    if (kk < 1) return fail(c, UCP_EINVAL, "ion_substep_ratio must be >= 1");
-    if (n_electron_steps < 0 || n_electron_steps % kk)
-        return fail(c, UCP_EINVAL, "n_electron_steps must be a non-negative multiple of k");
-    int rc = valid_walk_args(c, theta, eps);
-    if (rc) return rc;
+    int rc;
     if (!c->acc_valid) {
         if (!c->tree_valid && (rc = build(c))) return rc;
         if ((rc = force(c, theta, eps, 0, false))) return rc;
     }
     const double dt_i = (double)kk * dt_e;
     const double h_i = 0.5 * dt_i, h_e = 0.5 * dt_e;
-    int64_t nblocks = n_electron_steps / kk;
     int pend_i = 0, pend_e = 0;
     for (int64_t b = 0; b < nblocks; ++b) {
         int k = c->cur;
@@ -670,6 +668,11 @@ int ucp_step(ucp_ctx* c, double dt_e, int kk, int64_t n_electron_steps, double t
             // the walk over every particle also leaves phi for a following ucp_energy
             if ((rc = force(c, theta, eps, sub < kk, sub == kk))) return rc;
             pend_e = 1;
+            if (store) {
+                k = c->cur;
+                launch_scatter3(c->st[k][0], c->st[k][1], c->st[k][2], c->id[k], c->n,
+                                store + (size_t)3 * c->n * (size_t)(b * kk + sub - 1), c->s);
+            }
         }
         pend_i = 1;
         c->steps += kk;
@@ -682,6 +685,152 @@ int ucp_step(ucp_ctx* c, double dt_e, int kk, int64_t n_electron_steps, double t
         launch_kick(c->st[k][3], c->st[k][4], c->st[k][5], c->ax, c->ay, c->az, c->sp[k], UCP_ION,
                     h_i, c->n, 1, c->s);
     return check_launch(c, "step");
+}
+
+int ucp_step(ucp_ctx* c, double dt_e, int kk, int64_t n_electron_steps, double theta, double eps)
+{
+    if (!c) return UCP_EINVAL;
+    if (!c->have_state) return fail(c, UCP_ESTATE, "no state");
+    if (!(dt_e > 0.0) || !std::isfinite(dt_e)) return fail(c, UCP_EINVAL, "dt_e must be > 0");
+    if (kk < 1) return fail(c, UCP_EINVAL, "ion_substep_ratio must be >= 1");
+    if (n_electron_steps < 0 || n_electron_steps % kk)
+        return fail(c, UCP_EINVAL, "n_electron_steps must be a non-negative multiple of k");
+    int rc = valid_walk_args(c, theta, eps);
+    if (rc) return rc;
+    return run_blocks(c, dt_e, kk, n_electron_steps / kk, theta, eps, nullptr);
+}
+
+// Replace the positions and velocities (device, caller order) without the
+// checks of ucp_set_state; species stay as set.
+static void load_state(ucp_ctx* c, const double* dpos, const double* dvel)
+{
+    int k = c->cur;
+    launch_deinterleave(dpos, c->n, c->st[k][0], c->st[k][1], c->st[k][2], c->s);
+    launch_deinterleave(dvel, c->n, c->st[k][3], c->st[k][4], c->st[k][5], c->s);
+    cudaMemcpyAsync(c->sp[k], c->sp_caller, (size_t)c->n, cudaMemcpyDeviceToDevice, c->s);
+    launch_iota(c->id[k], c->n, c->s);
+    c->tree_valid = false;
+    c->acc_valid = false;
+    c->phi_valid = false;
+}
+
+int ucp_grad_ke_electrons(ucp_ctx* c, double dt_e, int kk, int64_t n_steps, double theta,
+                          double eps, int64_t checkpoint_every, double* loss, double* grad_x,
+                          double* grad_v, int on_device)
+{
+    if (!c) return UCP_EINVAL;
+    if (!c->have_state) return fail(c, UCP_ESTATE, "no state");
+    if (!(dt_e > 0.0) || !std::isfinite(dt_e) || kk < 1 || n_steps < kk || n_steps % kk ||
+        checkpoint_every < kk || checkpoint_every % kk)
+        return fail(c, UCP_EINVAL, "need k >= 1, n_steps and checkpoint_every multiples of k");
+    if (c->potential != UCP_POT_PLUMMER) return fail(c, UCP_EINVAL, "adjoint: Plummer law only");
+    int rc = valid_walk_args(c, theta, eps);
+    if (rc) return rc;
+    const size_t n3 = (size_t)3 * c->n;
+    const int64_t S = n_steps, C = checkpoint_every;
+    const int64_t nseg = (S + C - 1) / C;
+    // working memory of this call: checkpoints, one segment of positions, lambdas
+    double *ck = nullptr, *seg = nullptr, *lx = nullptr, *lv = nullptr, *lam = nullptr,
+           *lsorted = nullptr, *mu = nullptr, *adj = nullptr, *dloss = nullptr, *zero = nullptr;
+    auto freeall = [&]() {
+        for (double* p : {ck, seg, lx, lv, lam, lsorted, mu, adj, dloss, zero})
+            if (p) cudaFree(p);
+    };
+    size_t adj_words = (size_t)c->t.cap * 12;
+    if (cudaMalloc(&ck, sizeof(double) * n3 * 2 * (nseg + 1)) ||
+        cudaMalloc(&seg, sizeof(double) * n3 * (C + 1)) || cudaMalloc(&lx, sizeof(double) * n3) ||
+        cudaMalloc(&lv, sizeof(double) * n3) || cudaMalloc(&lam, sizeof(double) * n3) ||
+        cudaMalloc(&lsorted, sizeof(double) * n3) || cudaMalloc(&mu, sizeof(double) * n3) ||
+        cudaMalloc(&adj, sizeof(double) * adj_words) || cudaMalloc(&dloss, sizeof(double)) ||
+        cudaMalloc(&zero, sizeof(double) * n3)) {
+        cudaGetLastError();
+        freeall();
+        return fail(c, UCP_ENOMEM, "adjoint working memory");
+    }
+    auto snapshot = [&](double* dst) {
+        int k = c->cur;
+        launch_scatter3(c->st[k][0], c->st[k][1], c->st[k][2], c->id[k], c->n, dst, c->s);
+        launch_scatter3(c->st[k][3], c->st[k][4], c->st[k][5], c->id[k], c->n, dst + n3, c->s);
+    };
+    const double h_e = 0.5 * dt_e, h_i = 0.5 * (double)kk * dt_e;
+    int64_t steps0 = c->steps;
+    // forward, checkpoints at g = 0, C, 2C, ...
+    snapshot(ck);
+    for (int64_t sgi = 0; sgi < nseg; ++sgi) {
+        int64_t len = std::min(C, S - sgi * C);
+        if ((rc = run_blocks(c, dt_e, kk, len / kk, theta, eps, nullptr))) break;
+        snapshot(ck + 2 * n3 * (sgi + 1));
+    }
+    if (rc) {
+        freeall();
+        return rc;
+    }
+    launch_ke_seed(ck + 2 * n3 * nseg + n3, c->sp_caller, c->n, c->m[UCP_ELECTRON], lv, dloss,
+                   c->s);
+    cudaMemsetAsync(lx, 0, sizeof(double) * n3, c->s);
+    cudaMemsetAsync(zero, 0, sizeof(double) * n3, c->s);
+    WalkArgs a;
+    // reverse: for g = S .. 1: adjoint of the kicks at X_g, then of drift g; X_0 last
+    for (int64_t sgi = nseg - 1; sgi >= 0 && !rc; --sgi) {
+        const int64_t g0 = sgi * C, len = std::min(C, S - g0);
+        load_state(c, ck + 2 * n3 * sgi, ck + 2 * n3 * sgi + n3);
+        // seg[0] = X_{g0}; seg[j] = X_{g0 + j}
+        cudaMemcpyAsync(seg, ck + 2 * n3 * sgi, sizeof(double) * n3, cudaMemcpyDeviceToDevice,
+                        c->s);
+        if ((rc = run_blocks(c, dt_e, kk, len / kk, theta, eps, seg + n3))) break;
+        for (int64_t j = len; j >= (sgi == 0 ? 0 : 1); --j) {
+            const int64_t g = g0 + j;
+            // merged kicks that use a(X_g): electrons 2 h_e (1 at the ends), ions 2 h_i at
+            // block boundaries (1 at the ends), none inside a block
+            const bool endp = g == 0 || g == S;
+            const double ce = (endp ? 1.0 : 2.0) * h_e;
+            const double ci = (g % kk == 0) ? (endp ? 1.0 : 2.0) * h_i : 0.0;
+            load_state(c, seg + n3 * (size_t)j, zero);
+            if ((rc = build(c))) break;
+            launch_mac_prepare(c->t, c->cube, theta, 0, c->s);
+            int k = c->cur;
+            launch_kick_lambda(lv, c->sp_caller, c->n, ce, ci, lam, c->s);
+            launch_gather3(lam, c->id[k], c->n, lsorted, c->s);
+            a.x = c->st[k][0];
+            a.y = c->st[k][1];
+            a.z = c->st[k][2];
+            a.sp = c->sp[k];
+            a.qsp = c->qsp;
+            a.msp = c->msp;
+            a.src32 = nullptr;
+            a.t = c->t;
+            a.targets = nullptr;
+            a.ntargets = c->n;
+            a.chunks = c->chunks_all;
+            a.nchunks = c->n_chunks_all;
+            a.pos_off = c->pos_off;
+            a.eps2 = eps * eps;
+            a.kelbg = 0;
+            a.lambda = 1.0;
+            a.work = c->work;
+            launch_walk_adjoint(a, lsorted, mu, adj, c->t.cap, c->nsm, c->s);
+            launch_scatter_add3(mu, c->id[k], c->n, lx, c->s);
+            if (g > 0) launch_axpy3(lv, lx, dt_e, c->n, c->s);  // drift g
+            if ((rc = check_launch(c, "adjoint"))) break;
+        }
+    }
+    if (!rc) {
+        double L = 0.0;
+        cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+        if (grad_x && cudaMemcpyAsync(grad_x, lx, sizeof(double) * n3, kind, c->s)) rc = UCP_ECUDA;
+        if (grad_v && cudaMemcpyAsync(grad_v, lv, sizeof(double) * n3, kind, c->s)) rc = UCP_ECUDA;
+        if (cudaMemcpyAsync(&L, dloss, sizeof(double), cudaMemcpyDeviceToHost, c->s)) rc = UCP_ECUDA;
+        // leave the context at the end of the run
+        load_state(c, ck + 2 * n3 * nseg, ck + 2 * n3 * nseg + n3);
+        if (cudaStreamSynchronize(c->s)) rc = UCP_ECUDA;
+        if (loss) *loss = L;
+        c->steps = steps0 + S;
+        if (rc) fail(c, rc, "adjoint copies failed");
+    }
+    cudaStreamSynchronize(c->s);
+    freeall();
+    if (!rc) rc = device_error(c);
+    return rc;
 }
 
 int ucp_energy(ucp_ctx* c, double theta, double eps, double out[6])

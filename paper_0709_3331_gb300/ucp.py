@@ -25,7 +25,7 @@ EXPORTS = ("ucp_create", "ucp_destroy", "ucp_set_state", "ucp_get_state", "ucp_t
            "ucp_tree_force", "ucp_step", "ucp_energy", "ucp_stats", "ucp_get_cube",
            "ucp_get_sorted", "ucp_get_tree", "ucp_get_counts", "ucp_profile", "ucp_profile_read",
            "ucp_strerror", "ucp_last_error", "ucp_selftest_wait_timeout", "ucp_create_batch",
-           "ucp_energy_clouds", "ucp_get_cubes")
+           "ucp_energy_clouds", "ucp_get_cubes", "ucp_grad_ke_electrons")
 
 
 class UcpError(RuntimeError):
@@ -73,6 +73,9 @@ def lib():
         L.ucp_energy_clouds.restype = C.c_int
         L.ucp_get_cubes.argtypes = [vp, vp]
         L.ucp_get_cubes.restype = C.c_int
+        L.ucp_grad_ke_electrons.argtypes = [vp, dbl, i32, i64, dbl, dbl, i64, C.POINTER(dbl), vp,
+                                             vp, i32]
+        L.ucp_grad_ke_electrons.restype = C.c_int
         L.ucp_selftest_wait_timeout.argtypes = [vp]
         L.ucp_selftest_wait_timeout.restype = C.c_int
         L.ucp_strerror.argtypes = [i32]
@@ -207,6 +210,24 @@ class Context:
         self._check(lib().ucp_energy(self._h, float(theta), float(eps), out.ctypes.data),
                     "ucp_energy")
         return out
+
+    def grad_ke_electrons(self, dt_e, ion_substep_ratio, n_steps, theta, eps,
+                          checkpoint_every=None, grad_x=None, grad_v=None):
+        """(L, dL/dx0, dL/dv0) for L = electron kinetic energy after ``n_steps``
+        electron substeps from the current state (``ucp_grad_ke_electrons``)."""
+        if checkpoint_every is None:
+            checkpoint_every = n_steps
+        if grad_x is None and grad_v is None:
+            grad_x = np.empty((self.n, 3))
+            grad_v = np.empty((self.n, 3))
+        gx, d1 = _ptr(grad_x, np.float64)
+        gv, d2 = _ptr(grad_v, np.float64)
+        loss = C.c_double(0.0)
+        self._check(lib().ucp_grad_ke_electrons(self._h, float(dt_e), int(ion_substep_ratio),
+                                                int(n_steps), float(theta), float(eps),
+                                                int(checkpoint_every), C.byref(loss), gx, gv,
+                                                max(d1, d2)), "ucp_grad_ke_electrons")
+        return loss.value, grad_x, grad_v
 
     def energy_clouds(self, theta, eps):
         out = np.zeros((self.n_clouds, 6))

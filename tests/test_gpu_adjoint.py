@@ -1,0 +1,100 @@
+"""Reverse-mode gradient of the electron kinetic energy after a run
+(ucp_grad_ke_electrons): against the FP64 oracle's adjoint on the same inputs,
+against central finite differences of the GPU forward run, and through the
+torch.autograd front end."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_0709_3331_gb300.inputs import gaussian_cloud
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def U():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_0709_3331_gb300 import build as b
+    b.build()
+    import paper_0709_3331_gb300 as P
+    return P
+
+
+def rel_rms(a, b):
+    return math.sqrt(((a - b) ** 2).sum() / (b ** 2).sum())
+
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-6), (1, 1e-4)])
+@pytest.mark.parametrize("k,steps,ckpt", [(2, 6, 2), (3, 6, 6)])
+def test_gradient_vs_oracle(U, orc, prec, tol, k, steps, ckpt):
+    c = gaussian_cloud(2048, 1.0, 1)
+    theta, eps, lc, dt = 0.5, 0.01, 8, 1e-3
+    L_ref, gx_ref, gv_ref = orc.run_adjoint_ke_e(c.pos, c.vel, c.species, c.q, c.m, dt, k,
+                                                 steps // k, theta, eps, leaf_cap=lc, nthreads=4)
+    with U.Context(c.n, c.q, c.m, leaf_cap=lc, precision=prec) as ctx:
+        ctx.set_state(c.pos, c.vel, c.species)
+        L, gx, gv = ctx.grad_ke_electrons(dt, k, steps, theta, eps, ckpt)
+        p_end, _ = ctx.get_state()
+        p_ref, _, _ = orc.run(c.pos, c.vel, c.species, c.q, c.m, dt, k, steps // k, theta, eps,
+                              leaf_cap=lc)
+    assert L == pytest.approx(L_ref, rel=10 * tol)
+    assert rel_rms(gx, gx_ref) <= tol
+    assert rel_rms(gv, gv_ref) <= tol
+    assert np.abs(p_end - p_ref).max() < 1e-3   # the context ends after the run
+
+
+def test_gradient_vs_finite_differences(U):
+    c = gaussian_cloud(2048, 1.0, 1)
+    theta, eps, lc, dt, k, steps = 0.5, 0.01, 8, 1e-3, 2, 4
+    with U.Context(c.n, c.q, c.m, leaf_cap=lc, precision=0) as ctx:
+        ctx.set_state(c.pos, c.vel, c.species)
+        L, gx, gv = ctx.grad_ke_electrons(dt, k, steps, theta, eps, 2)
+
+        def loss(p, v):
+            ctx.set_state(p, v, c.species)
+            ctx.step(dt, k, steps, theta, eps)
+            _, vv = ctx.get_state()
+            e = c.species == 1
+            return 0.5 * c.m[1] * (vv[e] ** 2).sum()
+
+        assert loss(c.pos, c.vel) == pytest.approx(L, rel=1e-12)
+        rng = np.random.default_rng(3)
+        h = 1e-4
+        good, total = 0, 0
+        for _ in range(32):
+            i, a = int(rng.integers(c.n)), int(rng.integers(3))
+            for which, g in (("x", gx), ("v", gv)):
+                p, v = c.pos.copy(), c.vel.copy()
+                arr = p if which == "x" else v
+                arr[i, a] += h
+                lp = loss(p, v)
+                arr[i, a] -= 2 * h
+                lm = loss(p, v)
+                fd = (lp - lm) / (2 * h)
+                total += 1
+                # central differences with h = 1e-4 carry an O(h^2) error, and a box
+                # boundary or opening decision crossed by the step makes the tree jump
+                if abs(fd - g[i, a]) <= 1e-3 * abs(fd) + 1e-6 * abs(L):
+                    good += 1
+    assert good >= total - 3, (good, total)
+
+
+def test_autograd_front_end(U):
+    import torch
+    from paper_0709_3331_gb300.autograd import electron_ke_after_run
+    c = gaussian_cloud(1024, 1.0, 2)
+    dev = torch.device("cuda")
+    pos = torch.from_numpy(c.pos).to(dev).requires_grad_(True)
+    vel = torch.from_numpy(c.vel).to(dev).requires_grad_(True)
+    sp = torch.from_numpy(c.species).to(dev)
+    with U.Context(c.n, c.q, c.m, leaf_cap=8, precision=1) as ctx:
+        L = electron_ke_after_run(pos, vel, sp, ctx, 1e-3, 2, 4, 0.5, 0.01, 2)
+        (2.0 * L).backward()
+        ctx.set_state(c.pos, c.vel, c.species)
+        L2, gx, gv = ctx.grad_ke_electrons(1e-3, 2, 4, 0.5, 0.01, 2)
+    assert float(L) == pytest.approx(L2, rel=1e-12)
+    np.testing.assert_allclose(pos.grad.cpu().numpy(), 2.0 * gx, rtol=1e-9, atol=1e-12)
+    np.testing.assert_allclose(vel.grad.cpu().numpy(), 2.0 * gv, rtol=1e-9, atol=1e-12)
