@@ -477,6 +477,35 @@ def run_extras(c, W, ws, pos_d, vel_d, sp_d, Context, UCP_FP32C, UCP_FP64, timed
     torch.cuda.synchronize()
     mp = t0.elapsed_time(t1)
     e1 = cp.energy(0.5, W["eps"])
+    # differentiation form: N = 262144 (sigma 6), FP32C forces with FP64 state,
+    # gradient of the final electron kinetic energy w.r.t. the initial state
+    # (40 electron substeps, checkpoint every 20), against the forward alone
+    c4 = gaussian_cloud(262144, 6.0, 5)
+    ca = Context(c4.n, c4.q, c4.m, leaf_cap=W["leaf_cap"], precision=UCP_FP32C)
+    p4 = torch.from_numpy(c4.pos).cuda()
+    v4 = torch.from_numpy(c4.vel).cuda()
+    s4 = torch.from_numpy(c4.species).cuda()
+    gx4 = torch.empty_like(p4)
+    gv4 = torch.empty_like(v4)
+    ca.set_state(p4, v4, s4)
+    torch.cuda.synchronize()
+    w0 = time.perf_counter()
+    ca.step(W["dt_e"], W["k"], 40, 0.5, W["eps"])
+    torch.cuda.synchronize()
+    t_fwd = time.perf_counter() - w0
+    ca.set_state(p4, v4, s4)
+    torch.cuda.synchronize()
+    w0 = time.perf_counter()
+    L4, _, _ = ca.grad_ke_electrons(W["dt_e"], W["k"], 40, 0.5, W["eps"], 20, gx4, gv4)
+    torch.cuda.synchronize()
+    t_grad = time.perf_counter() - w0
+    extra["adjoint_n262144"] = {
+        "electron_steps": 40, "checkpoint_every": 20, "forward_s": t_fwd, "gradient_s": t_grad,
+        "gradient_over_forward": t_grad / t_fwd, "loss": L4,
+        "note": "gradient time includes the forward run, the checkpointed recomputation and "
+                "41 FP64 adjoint walks"}
+    ca.close()
+
     extra["plain_fp64_n131072"] = {
         "electron_steps": 100, "ms": mp, "particle_steps_per_s": c1.n * 100 / (mp / 1e3),
         "energy_drift": abs(e1[3] - e0[3]) / (e0[0] + e0[1] + abs(e0[2]))}

@@ -95,6 +95,6 @@ def test_autograd_front_end(U):
         (2.0 * L).backward()
         ctx.set_state(c.pos, c.vel, c.species)
         L2, gx, gv = ctx.grad_ke_electrons(1e-3, 2, 4, 0.5, 0.01, 2)
-    assert float(L) == pytest.approx(L2, rel=1e-12)
+    assert L.detach().item() == pytest.approx(L2, rel=1e-12)
     np.testing.assert_allclose(pos.grad.cpu().numpy(), 2.0 * gx, rtol=1e-9, atol=1e-12)
     np.testing.assert_allclose(vel.grad.cpu().numpy(), 2.0 * gv, rtol=1e-9, atol=1e-12)
