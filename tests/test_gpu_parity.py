@@ -399,3 +399,25 @@ def test_sec5_relaxation_short_run(U, orc, prec):
     t_ref, t_gpu = temps(v_ref), temps(vel)
     np.testing.assert_allclose(t_gpu, t_ref, rtol=1e-3)
     assert np.abs(pos - p_ref).max() < 1e-6 * np.abs(c.pos).max()
+
+
+def test_energy_drift_bounded_by_oracle(U, orc):
+    """The drift of the total energy over a short run stays within twice the
+    oracle's drift at the same step (or 1e-3): close encounters under-resolved by
+    dt make some drift intrinsic, so the oracle sets the bar."""
+    c = gaussian_cloud(2048, 1.0, 1)
+    theta, eps, lc, dt, k, steps = 0.5, 0.01, 8, 1e-3, 10, 100
+    e0 = orc.energy(c.pos, c.vel, c.species, c.q, c.m, theta, eps, leaf_cap=lc)
+    p, v, _ = orc.run(c.pos, c.vel, c.species, c.q, c.m, dt, k, steps // k, theta, eps,
+                      leaf_cap=lc, nthreads=4)
+    e1 = orc.energy(p, v, c.species, c.q, c.m, theta, eps, leaf_cap=lc)
+    scale = e0[0] + e0[1] + abs(e0[2])
+    drift_ref = abs(e1[3] - e0[3]) / scale
+    for prec in (0, 1):
+        with U.Context(c.n, c.q, c.m, leaf_cap=lc, precision=prec) as ctx:
+            ctx.set_state(c.pos, c.vel, c.species)
+            g0 = ctx.energy(theta, eps)
+            ctx.step(dt, k, steps, theta, eps)
+            g1 = ctx.energy(theta, eps)
+        drift = abs(g1[3] - g0[3]) / (g0[0] + g0[1] + abs(g0[2]))
+        assert drift <= max(2 * drift_ref, 1e-3), (prec, drift, drift_ref)
