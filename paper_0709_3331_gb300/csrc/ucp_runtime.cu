@@ -70,13 +70,9 @@ struct ucp_ctx {
     std::vector<int> cloud_start_h;    // n_clouds + 1
     int* cloud_start = nullptr;        // device copy
     unsigned char* cloud = nullptr;    // cloud of each slot (batches only)
-    int4* chunks_all = nullptr;        // walk chunks (<= 32 targets) over all particles
-    int4* chunks_e = nullptr;          // walk chunks (<= 32) over the compacted electrons
-    int4* chunks64_all = nullptr;      // the same with <= 64 targets (packed FP32C walk)
-    int4* chunks64_e = nullptr;
+    int4* chunks_all = nullptr;        // walk chunks over all particles
+    int4* chunks_e = nullptr;          // walk chunks over the compacted electrons
     int n_chunks_all = 0, n_chunks_e = 0, n_chunks_all_cap = 0;
-    int n_chunks64_all = 0, n_chunks64_e = 0;
-    bool packed_walk = false;          // FP32C with the Plummer law: 64 targets per warp
     int sorted_buf = 0;                // key[] / val[] buffer of the last sort
     std::vector<double> cloud_energy;  // per-cloud {KE_i, KE_e, PE, px, py, pz} of the last energy
     bool have_state = false, tree_valid = false, acc_valid = false;
@@ -240,14 +236,9 @@ int force(ucp_ctx* c, double theta, double eps, int electrons_only, bool want_ph
     a.stats = c->stats;
     cudaMemsetAsync(c->cnt_p2p, 0, sizeof(int) * (size_t)c->n, c->s);
     cudaMemsetAsync(c->cnt_m2p, 0, sizeof(int) * (size_t)c->n, c->s);
-    if (c->packed_walk) {
-        a.chunks = electrons_only ? c->chunks64_e : c->chunks64_all;
-        a.nchunks = electrons_only ? c->n_chunks64_e : c->n_chunks64_all;
-    }
     if (a.ntargets > 0) {
         prof_begin(c);
-        if (c->packed_walk) launch_walk_fp32c_x2(a, c->nsm, c->s);
-        else if (f32) launch_walk_fp32c(a, c->nsm, c->s);
+        if (f32) launch_walk_fp32c(a, c->nsm, c->s);
         else launch_walk_fp64(a, c->nsm, c->s);
         prof_end(c);
         c->walk_targets += a.ntargets;
@@ -267,28 +258,25 @@ int force(ucp_ctx* c, double theta, double eps, int electrons_only, bool want_ph
 // compacted electron list (electrons keep their cloud order under sorting).
 int build_chunks(ucp_ctx* c, const std::vector<int>& ne_per_cloud)
 {
-    for (int size : {32, 64}) {
-        std::vector<int4> all, el;
-        int e0 = 0;
-        for (int cl = 0; cl < c->n_clouds; ++cl) {
-            int b = c->cloud_start_h[cl], e = c->cloud_start_h[cl + 1];
-            for (int t = b; t < e; t += size) all.push_back(make_int4(t, std::min(size, e - t), cl, 0));
-            int ne = ne_per_cloud[cl];
-            for (int t = 0; t < ne; t += size)
-                el.push_back(make_int4(e0 + t, std::min(size, ne - t), cl, 0));
-            e0 += ne;
-        }
-        if ((int)all.size() > c->n_chunks_all_cap || (int)el.size() > c->n_chunks_all_cap)
-            return fail(c, UCP_EINVAL, "internal: chunk capacity");
-        int4* da = size == 32 ? c->chunks_all : c->chunks64_all;
-        int4* de = size == 32 ? c->chunks_e : c->chunks64_e;
-        (size == 32 ? c->n_chunks_all : c->n_chunks64_all) = (int)all.size();
-        (size == 32 ? c->n_chunks_e : c->n_chunks64_e) = (int)el.size();
-        CK(cudaMemcpyAsync(da, all.data(), sizeof(int4) * all.size(), cudaMemcpyHostToDevice, c->s));
-        if (!el.empty())
-            CK(cudaMemcpyAsync(de, el.data(), sizeof(int4) * el.size(), cudaMemcpyHostToDevice, c->s));
-        CK(cudaStreamSynchronize(c->s));
+    std::vector<int4> all, el;
+    int e0 = 0;
+    for (int cl = 0; cl < c->n_clouds; ++cl) {
+        int b = c->cloud_start_h[cl], e = c->cloud_start_h[cl + 1];
+        for (int t = b; t < e; t += 32) all.push_back(make_int4(t, std::min(32, e - t), cl, 0));
+        int ne = ne_per_cloud[cl];
+        for (int t = 0; t < ne; t += 32) el.push_back(make_int4(e0 + t, std::min(32, ne - t), cl, 0));
+        e0 += ne;
     }
+    if ((int)all.size() > c->n_chunks_all_cap || (int)el.size() > c->n_chunks_all_cap)
+        return fail(c, UCP_EINVAL, "internal: chunk capacity");
+    c->n_chunks_all = (int)all.size();
+    c->n_chunks_e = (int)el.size();
+    CK(cudaMemcpyAsync(c->chunks_all, all.data(), sizeof(int4) * all.size(), cudaMemcpyHostToDevice,
+                       c->s));
+    if (!el.empty())
+        CK(cudaMemcpyAsync(c->chunks_e, el.data(), sizeof(int4) * el.size(),
+                           cudaMemcpyHostToDevice, c->s));
+    CK(cudaStreamSynchronize(c->s));
     return UCP_OK;
 }
 
@@ -386,7 +374,6 @@ int ucp_create_batch(ucp_ctx** out, const ucp_params* p, int32_t n_clouds, const
     c->precision = p->precision;
     c->potential = p->potential;
     c->lambda_ei = p->potential == UCP_POT_KELBG ? p->lambda_ei : 1.0;
-    c->packed_walk = p->precision == UCP_FP32C && p->potential == UCP_POT_PLUMMER;
     for (int s = 0; s < 2; ++s) {
         c->q[s] = p->q[s];
         c->m[s] = p->m[s];
@@ -494,9 +481,7 @@ int ucp_create_batch(ucp_ctx** out, const ucp_params* p, int32_t n_clouds, const
         for (int i = 0; i < n_clouds; ++i) nch += (sizes[i] + 31) / 32;
         c->n_chunks_all_cap = (int)nch;
         if ((rc = dalloc(c, &c->chunks_all, (size_t)nch)) ||
-            (rc = dalloc(c, &c->chunks_e, (size_t)nch)) ||
-            (rc = dalloc(c, &c->chunks64_all, (size_t)nch)) ||
-            (rc = dalloc(c, &c->chunks64_e, (size_t)nch)))
+            (rc = dalloc(c, &c->chunks_e, (size_t)nch)))
             return bail(rc);
     }
     if ((rc = dalloc(c, &c->qsp, 2)) || (rc = dalloc(c, &c->msp, 2))) return bail(rc);

@@ -474,255 +474,6 @@ k_walk_fp32c(WalkArgs a)
     }
 }
 
-// ------------------------------------------------------------------ FP32C, 64 targets
-// The same walk with two key-adjacent targets per lane (64 per warp): the
-// criterion, the expansion and the pair loop run in packed FP32x2 arithmetic,
-// one element per target, so one instruction serves both targets and the
-// per-visit control is paid once for 64 targets.  Plummer law only.
-__device__ __forceinline__ float2 splat(float a) { return make_float2(a, a); }
-__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
-__device__ __forceinline__ float2 sub2(float2 a, float2 b)
-{
-    return __ffma2_rn(b, make_float2(-1.f, -1.f), a);
-}
-__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
-__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
-
-__device__ __forceinline__ void two_sum2(float2& s, float2& c, float2 v)
-{
-    float2 t = add2(s, v);
-    float2 bp = sub2(t, s);
-    float2 ap = sub2(t, bp);
-    c = add2(c, add2(sub2(s, ap), sub2(v, bp)));
-    s = t;
-}
-
-// expansion of one box on two targets (see m2p<float>); sel zeroes a target
-// that did not accept the box
-__device__ __forceinline__ void m2p_x2(float2 rx, float2 ry, float2 rz, float2 r2, float4 C,
-                                       float4 D, float4 E, float2 sel, float2& ex, float2& ey,
-                                       float2& ez, float2& ph)
-{
-    const float M = C.z, Dx = C.w, Dy = D.x, Dz = D.y;
-    const float Qxx = D.z, Qxy = D.w, Qxz = E.x, Qyy = E.y, Qyz = E.z, Qzz = E.w;
-    const float mhtr = -0.5f * (Qxx + Qyy + Qzz);
-    float2 g = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
-    g = mul2(g, sel);
-    float2 u = mul2(g, g);
-    float2 g3 = mul2(g, u);
-    float2 QRx = fma2(splat(Qxx), rx, fma2(splat(Qxy), ry, mul2(splat(Qxz), rz)));
-    float2 QRy = fma2(splat(Qxy), rx, fma2(splat(Qyy), ry, mul2(splat(Qyz), rz)));
-    float2 QRz = fma2(splat(Qxz), rx, fma2(splat(Qyz), ry, mul2(splat(Qzz), rz)));
-    float2 RQR = fma2(rx, QRx, fma2(ry, QRy, mul2(rz, QRz)));
-    float2 w = fma2(splat(Dx), rx, fma2(splat(Dy), ry, fma2(splat(Dz), rz, splat(mhtr))));
-    float2 h = mul2(u, RQR);
-    ph = fma2(g, fma2(u, fma2(splat(1.5f), h, w), splat(M)), ph);
-    float2 s3 = mul2(splat(3.f), u);
-    float2 aa = mul2(g3, fma2(s3, fma2(splat(2.5f), h, w), splat(M)));
-    float2 mg3 = mul2(splat(-1.f), g3);
-    ex = fma2(mg3, fma2(s3, QRx, splat(Dx)), fma2(aa, rx, ex));
-    ey = fma2(mg3, fma2(s3, QRy, splat(Dy)), fma2(aa, ry, ey));
-    ez = fma2(mg3, fma2(s3, QRz, splat(Dz)), fma2(aa, rz, ez));
-}
-
-struct WarpList2 {
-    int leaf[kList];
-    unsigned int mask0[kList];
-    unsigned int mask1[kList];
-};
-
-__global__ void __launch_bounds__(kWalkThreads, 4)
-k_walk_fp32c_x2(WalkArgs a)
-{
-    __shared__ WarpList2 L[kWalkWarps];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    WarpList2& lst = L[w];
-    const double q0 = a.qsp[0], q1 = a.qsp[1];
-    const float4* __restrict__ F = a.t.f32;
-    const float4* __restrict__ S = a.src32;
-    const float2 eps2 = splat((float)a.eps2);
-
-    for (int chunk = next_chunk(a.work, lane); chunk < a.nchunks;
-         chunk = next_chunk(a.work, lane)) {
-        // up to 64 key-consecutive targets of one cloud; lane l takes 2l and 2l + 1
-        const int4 ck = a.chunks[chunk];
-        const bool v0 = 2 * lane < ck.y, v1 = 2 * lane + 1 < ck.y;
-        const int i0 = ck.x + 2 * lane, i1 = i0 + 1;
-        const int t0 = v0 ? (a.targets ? a.targets[i0] : i0) : -1;
-        const int t1 = v1 ? (a.targets ? a.targets[i1] : i1) : -1;
-        const int root = a.pos_off[a.t.cloud_start ? a.t.cloud_start[ck.z] : 0];
-        const int end = __float_as_int(F[(size_t)root * kF32 + 1].w);
-        // targets as unevaluated float pairs x = xh + xl, element 0 / 1 = target t0 / t1
-        float2 xh = splat(0.f), yh = xh, zh = xh, xl = xh, yl = xh, zl = xh;
-        {
-            const double X0 = v0 ? a.x[t0] : 0.0, Y0 = v0 ? a.y[t0] : 0.0, Z0 = v0 ? a.z[t0] : 0.0;
-            const double X1 = v1 ? a.x[t1] : 0.0, Y1 = v1 ? a.y[t1] : 0.0, Z1 = v1 ? a.z[t1] : 0.0;
-            xh = make_float2((float)X0, (float)X1);
-            yh = make_float2((float)Y0, (float)Y1);
-            zh = make_float2((float)Z0, (float)Z1);
-            xl = make_float2((float)(X0 - (double)xh.x), (float)(X1 - (double)xh.y));
-            yl = make_float2((float)(Y0 - (double)yh.x), (float)(Y1 - (double)yh.y));
-            zl = make_float2((float)(Z0 - (double)zh.x), (float)(Z1 - (double)zh.y));
-        }
-        float2 sx = splat(0.f), sy = sx, sz = sx, sp = sx, cx = sx, cy = sx, cz = sx, cp = sx;
-        float2 bx = sx, by = sx, bz = sx, bp = sx;
-        int np0 = 0, np1 = 0, nm0 = 0, nm1 = 0, vis = 0;
-        int skip0 = v0 ? 0 : 0x7fffffff, skip1 = v1 ? 0 : 0x7fffffff;
-        int npl = 0;
-
-        auto fold_batch = [&]() {
-            two_sum2(sx, cx, bx);
-            two_sum2(sy, cy, by);
-            two_sum2(sz, cz, bz);
-            two_sum2(sp, cp, bp);
-            bx = by = bz = bp = splat(0.f);
-        };
-
-        auto flush = [&]() {
-            __syncwarp();
-            for (int e = 0; e < npl; ++e) {
-                const int nd = lst.leaf[e];
-                const bool in0 = (lst.mask0[e] >> lane) & 1u, in1 = (lst.mask1[e] >> lane) & 1u;
-                if (in0 || in1) {
-                    const float4* r = F + (size_t)nd * kF32;
-                    const float4 A = r[0], B = r[1], C = r[2];
-                    const float2 rx = add2(sub2(xh, splat(A.x)), sub2(xl, splat(B.x)));
-                    const float2 ry = add2(sub2(yh, splat(A.y)), sub2(yl, splat(B.y)));
-                    const float2 rz = add2(sub2(zh, splat(A.z)), sub2(zl, splat(B.z)));
-                    const int jb = __float_as_int(C.x), je = __float_as_int(C.y);
-                    float2 px = splat(0.f), py = px, pz = px, pp = px;
-                    // sources in pairs {x_2p, x_2p+1, y.., y..}, {z.., z.., q.., q..} as
-                    // offsets c_leaf - x_j; a source outside [jb, je), the target itself
-                    // or a target that did not open the leaf gets a zero inverse distance
-#pragma unroll 1
-                    for (int j = jb & ~1; j < je; j += 2) {
-                        const float4 P = __ldg(S + j), Q = __ldg(S + j + 1);
-#pragma unroll
-                        for (int h = 0; h < 2; ++h) {
-                            const int js = j + h;
-                            const float nx = h ? P.y : P.x, ny = h ? P.w : P.z;
-                            const float nz = h ? Q.y : Q.x, qj = h ? Q.w : Q.z;
-                            const bool okj = js >= jb && js < je;
-                            const float2 dx = add2(rx, splat(nx)), dy = add2(ry, splat(ny)),
-                                         dz = add2(rz, splat(nz));
-                            const float2 r2 = fma2(dx, dx, fma2(dy, dy, fma2(dz, dz, eps2)));
-                            const float2 ri = make_float2(
-                                (okj && in0 && js != t0) ? rsqrtf(r2.x) : 0.f,
-                                (okj && in1 && js != t1) ? rsqrtf(r2.y) : 0.f);
-                            const float2 qi = mul2(splat(qj), ri);
-                            const float2 qr3 = mul2(mul2(qi, ri), ri);
-                            px = fma2(qr3, dx, px);
-                            py = fma2(qr3, dy, py);
-                            pz = fma2(qr3, dz, pz);
-                            pp = add2(pp, qi);
-                        }
-                    }
-                    const int cnt = je - jb;
-                    if (in0) np0 += cnt - ((t0 >= jb && t0 < je) ? 1 : 0);
-                    if (in1) np1 += cnt - ((t1 >= jb && t1 < je) ? 1 : 0);
-                    two_sum2(sx, cx, px);
-                    two_sum2(sy, cy, py);
-                    two_sum2(sz, cz, pz);
-                    two_sum2(sp, cp, pp);
-                }
-            }
-            npl = 0;
-            __syncwarp();
-        };
-
-        int node = root;
-        while (node < end) {
-            const float4* r = F + (size_t)node * kF32;
-            const float4 A = r[0], B = r[1], C = r[2], D = r[3], E = r[4];
-            const int nxt = __float_as_int(B.w);
-            const bool leaf = __float_as_int(C.y) >= 0;
-            const bool act0 = node >= skip0, act1 = node >= skip1;
-            const float2 rx = add2(sub2(xh, splat(A.x)), sub2(xl, splat(B.x)));
-            const float2 ry = add2(sub2(yh, splat(A.y)), sub2(yl, splat(B.y)));
-            const float2 rz = add2(sub2(zh, splat(A.z)), sub2(zl, splat(B.z)));
-            const float2 d2 = fma2(rx, rx, fma2(ry, ry, mul2(rz, rz)));
-            bool acc0 = act0 && (A.w < d2.x);
-            bool acc1 = act1 && (A.w < d2.y);
-            // decisions within FP32 rounding of the threshold are retaken in FP64,
-            // exactly as the FP64 walk takes them
-            if (act0 && fabsf(d2.x - A.w) <= 4e-6f * d2.x) {
-                const double* m = a.t.mom + (size_t)node * kMom;
-                double dx = __dsub_rn(a.x[t0], m[0]), dy = __dsub_rn(a.y[t0], m[1]),
-                       dz = __dsub_rn(a.z[t0], m[2]);
-                acc0 = m[MR2] < __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)),
-                                          __dmul_rn(dz, dz));
-            }
-            if (act1 && fabsf(d2.y - A.w) <= 4e-6f * d2.y) {
-                const double* m = a.t.mom + (size_t)node * kMom;
-                double dx = __dsub_rn(a.x[t1], m[0]), dy = __dsub_rn(a.y[t1], m[1]),
-                       dz = __dsub_rn(a.z[t1], m[2]);
-                acc1 = m[MR2] < __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)),
-                                          __dmul_rn(dz, dz));
-            }
-            const bool opn0 = act0 && !acc0, opn1 = act1 && !acc1;
-            const unsigned int om0 = __ballot_sync(0xffffffffu, opn0);
-            const unsigned int om1 = __ballot_sync(0xffffffffu, opn1);
-            int next = nxt;
-            if (om0 | om1) {
-                if (leaf) {
-                    if (lane == 0) {
-                        lst.leaf[npl] = node;
-                        lst.mask0[npl] = om0;
-                        lst.mask1[npl] = om1;
-                    }
-                    ++npl;
-                } else {
-                    if (acc0) skip0 = nxt;
-                    if (acc1) skip1 = nxt;
-                    next = node + 1;
-                }
-            }
-            if (acc0 || acc1) {
-                m2p_x2(rx, ry, rz, add2(d2, eps2), C, D, E,
-                       make_float2(acc0 ? 1.f : 0.f, acc1 ? 1.f : 0.f), bx, by, bz, bp);
-                nm0 += acc0;
-                nm1 += acc1;
-            }
-            if ((++vis & (kM2PBatch - 1)) == 0) fold_batch();
-            node = next;
-            if (npl == kList) flush();
-        }
-        flush();
-        fold_batch();
-
-        if (v0) {
-            const int s = a.sp[t0];
-            const double qm = (s ? q1 : q0) / a.msp[s];
-            a.ax[t0] = qm * ((double)sx.x + (double)cx.x);
-            a.ay[t0] = qm * ((double)sy.x + (double)cy.x);
-            a.az[t0] = qm * ((double)sz.x + (double)cz.x);
-            if (a.phi) a.phi[t0] = (double)sp.x + (double)cp.x;
-            a.cnt_p2p[t0] = np0;
-            a.cnt_m2p[t0] = nm0;
-        }
-        if (v1) {
-            const int s = a.sp[t1];
-            const double qm = (s ? q1 : q0) / a.msp[s];
-            a.ax[t1] = qm * ((double)sx.y + (double)cx.y);
-            a.ay[t1] = qm * ((double)sy.y + (double)cy.y);
-            a.az[t1] = qm * ((double)sz.y + (double)cz.y);
-            if (a.phi) a.phi[t1] = (double)sp.y + (double)cp.y;
-            a.cnt_p2p[t1] = np1;
-            a.cnt_m2p[t1] = nm1;
-        }
-        unsigned long long sp2 = (unsigned long long)(np0 + np1), sm2 = (unsigned long long)(nm0 + nm1);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            sp2 += __shfl_xor_sync(0xffffffffu, sp2, o);
-            sm2 += __shfl_xor_sync(0xffffffffu, sm2, o);
-        }
-        if (lane == 0) {
-            atomicAdd(&a.stats[0], sp2);
-            atomicAdd(&a.stats[1], sm2);
-        }
-    }
-}
-
 // Per walk: rcrit2 = (s/theta + delta)^2 of every box in FP64 (theta = 0:
 // +inf, nothing accepted), and the FP32C box records.
 __global__ void k_mac_prepare(Tree t, const Cube* __restrict__ cube, double theta, int want_f32)
@@ -789,13 +540,6 @@ void launch_walk_fp32c(const WalkArgs& a, int nsm, cudaStream_t s)
     cudaMemsetAsync(a.work, 0, sizeof(int), s);
     if (a.kelbg) k_walk_fp32c<true><<<walk_blocks(a.nchunks, nsm, 12), kWalkThreads, 0, s>>>(a);
     else k_walk_fp32c<false><<<walk_blocks(a.nchunks, nsm, 12), kWalkThreads, 0, s>>>(a);
-}
-
-void launch_walk_fp32c_x2(const WalkArgs& a, int nsm, cudaStream_t s)
-{
-    count_launch(1);
-    cudaMemsetAsync(a.work, 0, sizeof(int), s);
-    k_walk_fp32c_x2<<<walk_blocks(a.nchunks, nsm, 8), kWalkThreads, 0, s>>>(a);
 }
 
 }  // namespace ucp
