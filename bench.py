@@ -503,7 +503,7 @@ def run_extras(c, W, ws, pos_d, vel_d, sp_d, Context, UCP_FP32C, UCP_FP64, timed
         "electron_steps": 40, "checkpoint_every": 20, "forward_s": t_fwd, "gradient_s": t_grad,
         "gradient_over_forward": t_grad / t_fwd, "loss": L4,
         "note": "gradient time includes the forward run, the checkpointed recomputation and "
-                "41 FP64 adjoint walks"}
+                "41 FP32 adjoint walks"}
     ca.close()
 
     extra["plain_fp64_n131072"] = {

@@ -130,7 +130,8 @@ int ucp_step(ucp_ctx* ctx, double dt_e, int ion_substep_ratio, int64_t n_electro
  * the end, grad_x = dL/dx0 and grad_v = dL/dv0 (N x 3, caller order; either may
  * be NULL).  Reverse mode: the discrete adjoint of every kick and drift, and at
  * every substep the adjoint of the TREE force with the tree held fixed (the same
- * boxes as the forward walk), evaluated in FP64; the state is kept every
+ * boxes as the forward walk), evaluated in FP64 (FP64 contexts) or in the FP32
+ * node-relative form with FP64 accumulation of the scatter (FP32C contexts); the state is kept every
  * checkpoint_every substeps (a multiple of k) and each stretch is recomputed
  * forward before it is reversed.  The context ends in the state after the run.
  * This call allocates its working memory (about (n_steps / checkpoint_every +

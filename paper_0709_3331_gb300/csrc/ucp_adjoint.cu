@@ -225,19 +225,227 @@ k_walk_adjoint(WalkArgs a, const double* __restrict__ lam, double* __restrict__ 
     }
 }
 
+// ---- FP32 form (FP32C contexts): the node-relative coordinates, records and
+// borderline FP64 decisions of the FP32C walk; per-lane sums in FP32, the
+// scatter into mu in FP64, the box accumulators in FP32.
+__device__ __forceinline__ float wsumf(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ float dot3f(const float* a, const float* b)
+{
+    return fmaf(a[0], b[0], fmaf(a[1], b[1], a[2] * b[2]));
+}
+
+__device__ __forceinline__ void qmulf(const float* Q, const float* v, float* o)
+{
+    o[0] = fmaf(Q[0], v[0], fmaf(Q[1], v[1], Q[2] * v[2]));
+    o[1] = fmaf(Q[1], v[0], fmaf(Q[3], v[1], Q[4] * v[2]));
+    o[2] = fmaf(Q[2], v[0], fmaf(Q[4], v[1], Q[5] * v[2]));
+}
+
+__device__ __forceinline__ void t4f(const float* R, const float* v, const float* Q, float g, float* o)
+{
+    float g2 = g * g, g5 = g2 * g2 * g, g7 = g5 * g2, g9 = g7 * g2;
+    float QR[3], Qv[3];
+    qmulf(Q, R, QR);
+    qmulf(Q, v, Qv);
+    float RQR = dot3f(R, QR), Rv = dot3f(R, v), vQR = dot3f(v, QR), trQ = Q[0] + Q[3] + Q[5];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+        o[a] = 105.f * R[a] * Rv * RQR * g9 -
+               15.f * g7 * (v[a] * RQR + 2.f * Rv * QR[a] + 2.f * R[a] * vQR + R[a] * Rv * trQ) +
+               3.f * g5 * (v[a] * trQ + 2.f * Qv[a]);
+}
+
+__global__ void __launch_bounds__(kAdjThreads)
+k_walk_adjoint_f32(WalkArgs a, const double* __restrict__ lam, double* __restrict__ mu,
+                   float* __restrict__ adj)
+{
+    __shared__ AdjList Ls[kAdjWarps];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    AdjList& lst = Ls[w];
+    const double q0 = a.qsp[0], q1 = a.qsp[1];
+    const float4* __restrict__ F = a.t.f32;
+    const float4* __restrict__ S = a.src32;
+    const float eps2 = (float)a.eps2;
+
+    for (int chunk = 0; true;) {
+        if (lane == 0) chunk = atomicAdd(a.work, 1);
+        chunk = __shfl_sync(0xffffffffu, chunk, 0);
+        if (chunk >= a.nchunks) break;
+        const int4 ck = a.chunks[chunk];
+        const bool valid = lane < ck.y;
+        const int t = valid ? ck.x + lane : -1;
+        const int root = a.pos_off[a.t.cloud_start ? a.t.cloud_start[ck.z] : 0];
+        const int end = __float_as_int(F[(size_t)root * kF32 + 1].w);
+        float xh = 0.f, yh = 0.f, zh = 0.f, xl = 0.f, yl = 0.f, zl = 0.f;
+        float l[3] = {0.f, 0.f, 0.f};
+        float qm = 0.f;
+        if (valid) {
+            double X = a.x[t], Y = a.y[t], Z = a.z[t];
+            xh = (float)X; yh = (float)Y; zh = (float)Z;
+            xl = (float)(X - (double)xh); yl = (float)(Y - (double)yh); zl = (float)(Z - (double)zh);
+            l[0] = (float)lam[3 * (size_t)t];
+            l[1] = (float)lam[3 * (size_t)t + 1];
+            l[2] = (float)lam[3 * (size_t)t + 2];
+            const int s = a.sp[t];
+            qm = (float)((s ? q1 : q0) / a.msp[s]);
+        }
+        const float wv[3] = {qm * l[0], qm * l[1], qm * l[2]};
+        float mt[3] = {0.f, 0.f, 0.f};
+        int skip = valid ? 0 : 0x7fffffff;
+        int npl = 0;
+
+        auto flush = [&]() {
+            __syncwarp();
+            for (int e = 0; e < npl; ++e) {
+                const int nd = lst.leaf[e];
+                const bool in = (lst.mask[e] >> lane) & 1u;
+                const float4* r = F + (size_t)nd * kF32;
+                const float4 A = r[0], B = r[1], C = r[2];
+                const float rx = (xh - A.x) + (xl - B.x), ry = (yh - A.y) + (yl - B.y),
+                            rz = (zh - A.z) + (zl - B.z);
+                const int jb = __float_as_int(C.x), je = __float_as_int(C.y);
+                for (int j = jb; j < je; ++j) {
+                    const float4 P = __ldg(S + (j & ~1)), Q = __ldg(S + (j & ~1) + 1);
+                    const bool odd = j & 1;
+                    float sx = 0.f, sy = 0.f, sz = 0.f;
+                    const float qj = odd ? Q.w : Q.z;
+                    if (in && j != t) {
+                        float r3[3] = {rx + (odd ? P.y : P.x), ry + (odd ? P.w : P.z),
+                                       rz + (odd ? Q.y : Q.x)};
+                        float g = rsqrtf(dot3f(r3, r3) + eps2);
+                        float g3 = g * g * g, g5 = g3 * g * g;
+                        float rl = dot3f(r3, l), rw = dot3f(r3, wv);
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) {
+                            mt[c] = fmaf(qm * qj, l[c] * g3 - 3.f * r3[c] * rl * g5, mt[c]);
+                        }
+                        sx = -qj * (wv[0] * g3 - 3.f * r3[0] * rw * g5);
+                        sy = -qj * (wv[1] * g3 - 3.f * r3[1] * rw * g5);
+                        sz = -qj * (wv[2] * g3 - 3.f * r3[2] * rw * g5);
+                    }
+                    sx = wsumf(sx);
+                    sy = wsumf(sy);
+                    sz = wsumf(sz);
+                    if (lane == 0) {
+                        atomicAdd(&mu[3 * (size_t)j], (double)sx);
+                        atomicAdd(&mu[3 * (size_t)j + 1], (double)sy);
+                        atomicAdd(&mu[3 * (size_t)j + 2], (double)sz);
+                    }
+                }
+            }
+            npl = 0;
+            __syncwarp();
+        };
+
+        int node = root;
+        while (node < end) {
+            const float4* r = F + (size_t)node * kF32;
+            const float4 A = r[0], B = r[1], C = r[2];
+            const int nxt = __float_as_int(B.w);
+            const bool leaf = __float_as_int(C.y) >= 0;
+            const bool active = node >= skip;
+            const float R[3] = {(xh - A.x) + (xl - B.x), (yh - A.y) + (yl - B.y),
+                                (zh - A.z) + (zl - B.z)};
+            const float d2 = dot3f(R, R);
+            bool acc = active && (A.w < d2);
+            if (active && fabsf(d2 - A.w) <= 4e-6f * d2) {
+                const double* m = a.t.mom + (size_t)node * kMom;
+                double dx = __dsub_rn(a.x[t], m[0]), dy = __dsub_rn(a.y[t], m[1]),
+                       dz = __dsub_rn(a.z[t], m[2]);
+                acc = m[MR2] < __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)),
+                                         __dmul_rn(dz, dz));
+            }
+            const bool opn = active && !acc;
+            const unsigned int am = __ballot_sync(0xffffffffu, acc);
+            const unsigned int om = __ballot_sync(0xffffffffu, opn);
+            int next = nxt;
+            if (om) {
+                if (leaf) {
+                    if (lane == 0) {
+                        lst.leaf[npl] = node;
+                        lst.mask[npl] = om;
+                    }
+                    ++npl;
+                } else {
+                    if (acc) skip = nxt;
+                    next = node + 1;
+                }
+            }
+            if (am) {
+                float src[12];
+#pragma unroll
+                for (int k = 0; k < 12; ++k) src[k] = 0.f;
+                if (acc) {
+                    const float4 D4 = r[3], E4 = r[4];
+                    const float M = C.z;
+                    const float D[3] = {C.w, D4.x, D4.y};
+                    const float Q[6] = {D4.z, D4.w, E4.x, E4.y, E4.z, E4.w};
+                    const float g = rsqrtf(d2 + eps2);
+                    const float g2 = g * g, g3 = g2 * g, g5 = g3 * g2, g7 = g5 * g2;
+                    const float Rl = dot3f(R, l), RD = dot3f(R, D), lD = dot3f(l, D);
+                    float T4l[3];
+                    t4f(R, l, Q, g, T4l);
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        float hess = M * (3.f * R[c] * Rl * g5 - l[c] * g3);
+                        float dterm = -15.f * R[c] * Rl * RD * g7 +
+                                      3.f * (l[c] * RD + D[c] * Rl + R[c] * lD) * g5;
+                        mt[c] -= qm * (hess - dterm + 0.5f * T4l[c]);
+                    }
+                    const float Rw = dot3f(R, wv);
+                    float T4w[3];
+                    t4f(R, wv, Q, g, T4w);
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        src[c] = 3.f * R[c] * Rw * g5 - wv[c] * g3;
+                        src[9 + c] = 0.5f * T4w[c];
+                    }
+                    const int ia[6] = {0, 0, 0, 1, 1, 2}, ib[6] = {0, 1, 2, 1, 2, 2};
+#pragma unroll
+                    for (int k = 0; k < 6; ++k) {
+                        const int e = ia[k], c = ib[k];
+                        src[3 + k] = -15.f * Rw * R[e] * R[c] * g7 +
+                                     3.f * (wv[e] * R[c] + wv[c] * R[e] + (e == c ? Rw : 0.f)) * g5;
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < 12; ++k) src[k] = wsumf(src[k]);
+                if (lane == 0)
+                    for (int k = 0; k < 12; ++k) atomicAdd(&adj[(size_t)node * 12 + k], src[k]);
+            }
+            node = next;
+            if (npl == kAdjList) flush();
+        }
+        flush();
+        if (valid) {
+            atomicAdd(&mu[3 * (size_t)t], (double)mt[0]);
+            atomicAdd(&mu[3 * (size_t)t + 1], (double)mt[1]);
+            atomicAdd(&mu[3 * (size_t)t + 2], (double)mt[2]);
+        }
+    }
+}
+
 // Every particle of a leaf receives the source-side terms of the leaf and of
 // all its ancestors: q_s (sum alpha - sum Gamma (x_s - c)) + |q_s| sum kappa / S0.
+template <class TA>
 __global__ void k_adjoint_push(const double* __restrict__ x, const double* __restrict__ y,
                                const double* __restrict__ z, const int8_t* __restrict__ sp,
                                const double* __restrict__ qsp, Tree t,
-                               const double* __restrict__ adj, double* __restrict__ mu)
+                               const TA* __restrict__ adj, double* __restrict__ mu)
 {
     const int nl = t.count[kMaxDepth + 1];
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nl; i += gridDim.x * blockDim.x) {
         const int leaf = t.leaf_list[i];
         double A[3] = {0, 0, 0}, G[6] = {0, 0, 0, 0, 0, 0}, Cc[3] = {0, 0, 0}, K[3] = {0, 0, 0};
         for (int nd = leaf; nd >= 0; nd = t.info[nd].w) {
-            const double* r = adj + (size_t)nd * 12;
+            double r[12];
+            for (int k = 0; k < 12; ++k) r[k] = (double)adj[(size_t)nd * 12 + k];
             const double* m = t.mom + (size_t)nd * kMom;
             double c[3] = {m[MC], m[MC + 1], m[MC + 2]};
             double Gc[3];
@@ -262,12 +470,13 @@ __global__ void k_adjoint_push(const double* __restrict__ x, const double* __res
     }
 }
 
-__global__ void k_zero_adj(const int* __restrict__ nnodes, double* __restrict__ adj)
+template <class TA>
+__global__ void k_zero_adj(const int* __restrict__ nnodes, TA* __restrict__ adj)
 {
     const size_t total = (size_t)*nnodes * 12;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
          i += (size_t)gridDim.x * blockDim.x)
-        adj[i] = 0.0;
+        adj[i] = (TA)0;
 }
 
 // dst[t] = src[id[t]] for N x 3 arrays (caller order -> key order)
@@ -376,13 +585,22 @@ void launch_walk_adjoint(const WalkArgs& a, const double* lam, double* mu, doubl
     count_launch(3);
     (void)nn_cap;
     cudaMemsetAsync(a.work, 0, sizeof(int), s);
-    k_zero_adj<<<2 * 152, 256, 0, s>>>(a.t.nnodes, adj);
     cudaMemsetAsync(mu, 0, sizeof(double) * 3 * (size_t)a.ntargets, s);
     int blocks = nsm * 8;
     int need = (a.nchunks + kAdjWarps - 1) / kAdjWarps;
     if (blocks > need) blocks = need;
-    k_walk_adjoint<<<blocks < 1 ? 1 : blocks, kAdjThreads, 0, s>>>(a, lam, mu, adj);
-    k_adjoint_push<<<4 * 152, 256, 0, s>>>(a.x, a.y, a.z, a.sp, a.qsp, a.t, adj, mu);
+    if (blocks < 1) blocks = 1;
+    if (a.src32) {
+        // FP32C context: FP32 walk, FP32 box accumulators (in the same buffer)
+        float* adjf = reinterpret_cast<float*>(adj);
+        k_zero_adj<float><<<2 * 152, 256, 0, s>>>(a.t.nnodes, adjf);
+        k_walk_adjoint_f32<<<blocks, kAdjThreads, 0, s>>>(a, lam, mu, adjf);
+        k_adjoint_push<float><<<4 * 152, 256, 0, s>>>(a.x, a.y, a.z, a.sp, a.qsp, a.t, adjf, mu);
+    } else {
+        k_zero_adj<double><<<2 * 152, 256, 0, s>>>(a.t.nnodes, adj);
+        k_walk_adjoint<<<blocks, kAdjThreads, 0, s>>>(a, lam, mu, adj);
+        k_adjoint_push<double><<<4 * 152, 256, 0, s>>>(a.x, a.y, a.z, a.sp, a.qsp, a.t, adj, mu);
+    }
 }
 
 }  // namespace ucp

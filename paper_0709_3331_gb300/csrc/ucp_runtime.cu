@@ -787,7 +787,8 @@ int ucp_grad_ke_electrons(ucp_ctx* c, double dt_e, int kk, int64_t n_steps, doub
             const double ci = (g % kk == 0) ? (endp ? 1.0 : 2.0) * h_i : 0.0;
             load_state(c, seg + n3 * (size_t)j, zero);
             if ((rc = build(c))) break;
-            launch_mac_prepare(c->t, c->cube, theta, 0, c->s);
+            const int f32 = c->precision == UCP_FP32C;
+            launch_mac_prepare(c->t, c->cube, theta, f32, c->s);
             int k = c->cur;
             launch_kick_lambda(lv, c->sp_caller, c->n, ce, ci, lam, c->s);
             launch_gather3(lam, c->id[k], c->n, lsorted, c->s);
@@ -797,7 +798,7 @@ int ucp_grad_ke_electrons(ucp_ctx* c, double dt_e, int kk, int64_t n_steps, doub
             a.sp = c->sp[k];
             a.qsp = c->qsp;
             a.msp = c->msp;
-            a.src32 = nullptr;
+            a.src32 = f32 ? c->src32 : nullptr;  // FP32C: the FP32 adjoint walk
             a.t = c->t;
             a.targets = nullptr;
             a.ntargets = c->n;
