@@ -142,6 +142,14 @@ int ucp_grad_ke_electrons(ucp_ctx* ctx, double dt_e, int ion_substep_ratio, int6
                           double theta, double eps, int64_t checkpoint_every, double* loss,
                           double* grad_x, double* grad_v, int on_device);
 
+/* enable != 0: ucp_step runs every block of k electron substeps as one CUDA graph,
+ * captured on a private stream the first time a block with these (k, dt_e, theta,
+ * eps) starts from a given state buffer, and replayed on the context's stream
+ * afterwards (the results are identical to the stream-ordered launches; kernel
+ * timing with ucp_profile turns it off).  Useful where launch overhead matters
+ * (small clouds, ensembles). */
+int ucp_set_graphs(ucp_ctx* ctx, int enable);
+
 /* Sec. 5 observables of the current state: out = {KE_ion, KE_electron, PE,
  * E = KE + PE, |P| (total momentum), electron steps taken}.  PE is
  * (1/2) sum_t q_t phi_t with the tree potential; the walk over all particles

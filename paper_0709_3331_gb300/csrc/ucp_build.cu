@@ -267,10 +267,16 @@ k_sort_hist_all(const unsigned long long* __restrict__ key, int n, unsigned int*
 }
 
 // goff[p][d] = number of keys whose pass-p digit is below d.
+// Also advances the sort's tag: every build's published words carry a tag 16
+// above the previous build's, kept on the device so that a captured graph
+// replays with fresh tags (every word of a pass region is rewritten each build,
+// so a stale word always carries an older tag, also across 30-bit wrap-around).
 __global__ void __launch_bounds__(kRadix) k_sort_offsets(const unsigned int* __restrict__ ghist,
-                                                         unsigned int* __restrict__ goff)
+                                                         unsigned int* __restrict__ goff,
+                                                         unsigned int* __restrict__ epoch)
 {
     __shared__ int tot;
+    if (threadIdx.x == 0) *epoch = (*epoch + 16u) & 0x3fffffffu;
     for (int p = 0; p < 8; ++p) {
         int v = (int)ghist[p * kRadix + threadIdx.x];
         goff[p * kRadix + threadIdx.x] = (unsigned int)block_excl_scan(v, &tot);
@@ -290,9 +296,10 @@ __global__ void __launch_bounds__(kSortThreads)
 k_onesweep(const unsigned long long* __restrict__ kin, const unsigned int* __restrict__ vin,
            unsigned long long* __restrict__ kout, unsigned int* __restrict__ vout, int n,
            int shift, const unsigned int* __restrict__ goff, unsigned long long* status,
-           int* tile_ctr, unsigned int epoch, int* err, int spin_limit,
-           const unsigned char* __restrict__ digit_of_val)
+           int* tile_ctr, const unsigned int* __restrict__ epoch_dev, unsigned int pass, int* err,
+           int spin_limit, const unsigned char* __restrict__ digit_of_val)
 {
+    const unsigned int epoch = (*epoch_dev + pass) & 0x3fffffffu;
     __shared__ int cnt[kSortWarps][kRadix];
     __shared__ int s_tile, s_fail;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -937,7 +944,7 @@ size_t sort_status_words(int n)
 }
 
 int launch_sort(unsigned long long* key[2], unsigned int* val[2], int n, SortScratch sc,
-                const unsigned int* ids_in, unsigned int epoch0, const unsigned char* cloud,
+                const unsigned int* ids_in, const unsigned char* cloud,
                 const int* cloud_start, int n_clouds, cudaStream_t s)
 {
     count_launch(11 + (n_clouds > 1 ? 1 : 0));
@@ -946,14 +953,14 @@ int launch_sort(unsigned long long* key[2], unsigned int* val[2], int n, SortScr
     int hb = (n + 4 * kSortThreads - 1) / (4 * kSortThreads);
     if (hb > 2 * 152) hb = 2 * 152;
     k_sort_hist_all<<<hb > 0 ? hb : 1, kSortThreads, 0, s>>>(key[0], n, sc.ghist);
-    k_sort_offsets<<<1, kRadix, 0, s>>>(sc.ghist, sc.goff);
+    k_sort_offsets<<<1, kRadix, 0, s>>>(sc.ghist, sc.goff, sc.epoch);
     int* tiles = reinterpret_cast<int*>(sc.ghist + 8 * kRadix);
     int cur = 0;
     for (int p = 0; p < 8; ++p) {
         k_onesweep<<<nb, kSortThreads, 0, s>>>(key[cur], val[cur], key[cur ^ 1], val[cur ^ 1], n,
                                                8 * p, sc.goff + p * kRadix,
                                                sc.status + (size_t)p * nb * kRadix, tiles + p,
-                                               epoch0 + (unsigned int)p, sc.err, kSortSpinLimit,
+                                               sc.epoch, (unsigned int)p, sc.err, kSortSpinLimit,
                                                nullptr);
         cur ^= 1;
     }
@@ -963,7 +970,7 @@ int launch_sort(unsigned long long* key[2], unsigned int* val[2], int n, SortScr
         k_onesweep<<<nb, kSortThreads, 0, s>>>(key[cur], val[cur], key[cur ^ 1], val[cur ^ 1], n,
                                                0, reinterpret_cast<const unsigned int*>(cloud_start),
                                                sc.status + (size_t)8 * nb * kRadix, tiles + 8,
-                                               epoch0 + 8u, sc.err, kSortSpinLimit, cloud);
+                                               sc.epoch, 8u, sc.err, kSortSpinLimit, cloud);
         cur ^= 1;
     }
     k_tiefix<<<(n + 255) / 256, 256, 0, s>>>(key[cur], val[cur], ids_in, n);
@@ -980,13 +987,14 @@ int sort_selftest_timeout(SortScratch sc, cudaStream_t s)
     if (cudaMemsetAsync(sc.status, 0, sizeof(unsigned long long) * 2 * kRadix, s) != cudaSuccess ||
         cudaMemcpyAsync(tiles, &one, sizeof(int), cudaMemcpyHostToDevice, s) != cudaSuccess ||
         cudaMemsetAsync(sc.goff, 0, sizeof(unsigned int) * kRadix, s) != cudaSuccess ||
+        cudaMemcpyAsync(sc.test_epoch, &one, sizeof(int), cudaMemcpyHostToDevice, s) != cudaSuccess ||
         cudaMemsetAsync(sc.test_keys, 0, sizeof(unsigned long long) * 4 * kSortTile, s) != cudaSuccess ||
         cudaMemsetAsync(sc.test_vals, 0, sizeof(unsigned int) * 4 * kSortTile, s) != cudaSuccess)
         return -1;
     // input: tiles 0-1 of the test buffers; output: tiles 2-3
     k_onesweep<<<1, kSortThreads, 0, s>>>(sc.test_keys, sc.test_vals, sc.test_keys + 2 * kSortTile,
                                           sc.test_vals + 2 * kSortTile, 2 * kSortTile, 0, sc.goff,
-                                          sc.status, tiles, 1u, sc.err, 2000, nullptr);
+                                          sc.status, tiles, sc.test_epoch, 0u, sc.err, 2000, nullptr);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

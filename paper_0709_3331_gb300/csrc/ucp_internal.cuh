@@ -70,6 +70,8 @@ struct SortScratch {
     unsigned int* goff;            // 8 x 256 digit offsets
     unsigned long long* status;    // 9 passes x tiles x 256 published words
     int* err;                      // raised by a wait that gave up
+    unsigned int* epoch;           // tag of the published words, advanced every build
+    unsigned int* test_epoch;      // tag used by the bounded-wait self-test (1)
     unsigned long long* test_keys; // 4 tiles, for the bounded-wait self-test
     unsigned int* test_vals;
 };
@@ -77,7 +79,7 @@ size_t sort_status_words(int n);
 size_t sort_test_words();
 // returns the buffer (0 or 1) that holds the sorted keys and permutation
 int launch_sort(unsigned long long* key[2], unsigned int* val[2], int n, SortScratch sc,
-                const unsigned int* ids_in, unsigned int epoch0, const unsigned char* cloud,
+                const unsigned int* ids_in, const unsigned char* cloud,
                 const int* cloud_start, int n_clouds, cudaStream_t s);
 int sort_selftest_timeout(SortScratch sc, cudaStream_t s);
 void launch_tiefix(const unsigned long long* key, unsigned int* perm, const unsigned int* ids,

@@ -80,7 +80,17 @@ struct ucp_ctx {
     double phi_theta = -1.0, phi_eps = -1.0;
     int64_t steps = 0, walk_targets = 0, walk_launches = 0;
     unsigned long long launch_base = 0;
-    unsigned int sort_epoch = 16;     // tags of the sort's published words (16 per build)
+
+    // captured blocks of the split-step push (ucp_set_graphs)
+    struct GraphEntry {
+        int kk, cur_in, cur_out;
+        double dt_e, theta, eps;
+        cudaGraphExec_t exec;
+        unsigned long long launches;
+    };
+    bool use_graphs = false;
+    cudaStream_t cap_stream = nullptr;
+    std::vector<GraphEntry> graphs;
 
     bool prof = false;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
@@ -172,9 +182,8 @@ int build(ucp_ctx* c)
                 cs, c->n_clouds, c->s);
     launch_keys(c->st[k][0], c->st[k][1], c->st[k][2], n, c->cube, c->t.cloud, c->key[0],
                 c->val[0], c->s);
-    const int b = launch_sort(c->key, c->val, n, c->sort, c->id[k], c->sort_epoch, c->t.cloud,
-                              c->cloud_start, c->n_clouds, c->s);
-    c->sort_epoch += 16;
+    const int b = launch_sort(c->key, c->val, n, c->sort, c->id[k], c->t.cloud, c->cloud_start,
+                              c->n_clouds, c->s);
     c->sorted_buf = b;
     const double* src[6];
     double* dst[6];
@@ -328,6 +337,8 @@ void ucp_destroy(ucp_ctx* c)
         cudaEventDestroy(e.first);
         cudaEventDestroy(e.second);
     }
+    for (auto& g : c->graphs) cudaGraphExecDestroy(g.exec);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     delete c;
 }
 
@@ -401,12 +412,14 @@ int ucp_create_batch(ucp_ctx** out, const ucp_params* p, int32_t n_clouds, const
         return bail(rc);
     if ((rc = dalloc(c, &c->sort.ghist, 8 * 256 + 9)) || (rc = dalloc(c, &c->sort.goff, 8 * 256)) ||
         (rc = dalloc(c, &c->sort.status, sort_status_words(c->n))) ||
-        (rc = dalloc(c, &c->sort.err, 1)) ||
+        (rc = dalloc(c, &c->sort.err, 1)) || (rc = dalloc(c, &c->sort.epoch, 1)) ||
+        (rc = dalloc(c, &c->sort.test_epoch, 1)) ||
         (rc = dalloc(c, &c->sort.test_keys, sort_test_words())) ||
         (rc = dalloc(c, &c->sort.test_vals, sort_test_words())))
         return bail(rc);
     if (cudaMemsetAsync(c->sort.status, 0, 8 * sort_status_words(c->n), c->s) != cudaSuccess ||
-        cudaMemsetAsync(c->sort.err, 0, sizeof(int), c->s) != cudaSuccess)
+        cudaMemsetAsync(c->sort.err, 0, sizeof(int), c->s) != cudaSuccess ||
+        cudaMemsetAsync(c->sort.epoch, 0, sizeof(unsigned int), c->s) != cudaSuccess)
         return bail(UCP_ECUDA);
     size_t spw = scan_partials_words(c->n);
     if ((rc = dalloc(c, &c->scan_part, spw))) return bail(rc);
@@ -687,6 +700,73 @@ static int run_blocks(ucp_ctx* c, double dt_e, int kk, int64_t nblocks, double t
     return check_launch(c, "step");
 }
 
+// One block of the push as a CUDA graph: captured on first use for (k, dt_e,
+// theta, eps, buffer parity) on a private stream, replayed on the context's
+// stream afterwards.  The block body is run_blocks with one block (no kick
+// fusion across blocks, which changes no result).
+static int run_block_graph(ucp_ctx* c, double dt_e, int kk, double theta, double eps)
+{
+    ucp_ctx::GraphEntry* hit = nullptr;
+    for (auto& g : c->graphs)
+        if (g.kk == kk && g.cur_in == c->cur && g.dt_e == dt_e && g.theta == theta && g.eps == eps)
+            hit = &g;
+    if (!hit) {
+        if (!c->cap_stream && cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking))
+            return fail(c, UCP_ECUDA, "capture stream");
+        const int cur0 = c->cur;
+        const int64_t steps0 = c->steps, wt0 = c->walk_targets, wl0 = c->walk_launches;
+        cudaStream_t orig = c->s;
+        c->s = c->cap_stream;
+        const unsigned long long l0 = g_launches.load();
+        cudaGraph_t graph = nullptr;
+        int rc = UCP_OK;
+        if (cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal)) {
+            c->s = orig;
+            return fail(c, UCP_ECUDA, "begin capture");
+        }
+        rc = run_blocks(c, dt_e, kk, 1, theta, eps, nullptr);
+        cudaError_t ec = cudaStreamEndCapture(c->cap_stream, &graph);
+        c->s = orig;
+        const unsigned long long nl = g_launches.load() - l0;
+        g_launches.fetch_sub(nl);
+        const int cur1 = c->cur;
+        c->cur = cur0;
+        c->steps = steps0;
+        c->walk_targets = wt0;
+        c->walk_launches = wl0;
+        if (rc || ec != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            cudaGetLastError();
+            return rc ? rc : fail(c, UCP_ECUDA, "capture of a step block failed");
+        }
+        cudaGraphExec_t exec = nullptr;
+        ec = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ec != cudaSuccess) return fail(c, UCP_ECUDA, "graph instantiation failed");
+        c->graphs.push_back({kk, cur0, cur1, dt_e, theta, eps, exec, nl});
+        hit = &c->graphs.back();
+    }
+    CK(cudaGraphLaunch(hit->exec, c->s));
+    count_launch((int)hit->launches);
+    c->cur = hit->cur_out;
+    c->steps += kk;
+    c->tree_valid = true;
+    c->acc_valid = true;
+    c->phi_valid = true;
+    c->phi_theta = theta;
+    c->phi_eps = eps;
+    c->walk_launches += kk;
+    c->walk_targets += (int64_t)(kk - 1) * c->n_e + c->n;
+    return UCP_OK;
+}
+
+int ucp_set_graphs(ucp_ctx* c, int enable)
+{
+    if (!c) return UCP_EINVAL;
+    c->use_graphs = enable != 0;
+    return UCP_OK;
+}
+
 int ucp_step(ucp_ctx* c, double dt_e, int kk, int64_t n_electron_steps, double theta, double eps)
 {
     if (!c) return UCP_EINVAL;
@@ -697,7 +777,15 @@ int ucp_step(ucp_ctx* c, double dt_e, int kk, int64_t n_electron_steps, double t
         return fail(c, UCP_EINVAL, "n_electron_steps must be a non-negative multiple of k");
     int rc = valid_walk_args(c, theta, eps);
     if (rc) return rc;
-    return run_blocks(c, dt_e, kk, n_electron_steps / kk, theta, eps, nullptr);
+    if (!c->use_graphs || c->prof) return run_blocks(c, dt_e, kk, n_electron_steps / kk, theta, eps,
+                                                     nullptr);
+    if (!c->acc_valid) {
+        if (!c->tree_valid && (rc = build(c))) return rc;
+        if ((rc = force(c, theta, eps, 0, false))) return rc;
+    }
+    for (int64_t b = 0; b < n_electron_steps / kk; ++b)
+        if ((rc = run_block_graph(c, dt_e, kk, theta, eps))) return rc;
+    return UCP_OK;
 }
 
 // Replace the positions and velocities (device, caller order) without the

@@ -25,7 +25,7 @@ EXPORTS = ("ucp_create", "ucp_destroy", "ucp_set_state", "ucp_get_state", "ucp_t
            "ucp_tree_force", "ucp_step", "ucp_energy", "ucp_stats", "ucp_get_cube",
            "ucp_get_sorted", "ucp_get_tree", "ucp_get_counts", "ucp_profile", "ucp_profile_read",
            "ucp_strerror", "ucp_last_error", "ucp_selftest_wait_timeout", "ucp_create_batch",
-           "ucp_energy_clouds", "ucp_get_cubes", "ucp_grad_ke_electrons")
+           "ucp_energy_clouds", "ucp_get_cubes", "ucp_grad_ke_electrons", "ucp_set_graphs")
 
 
 class UcpError(RuntimeError):
@@ -76,6 +76,8 @@ def lib():
         L.ucp_grad_ke_electrons.argtypes = [vp, dbl, i32, i64, dbl, dbl, i64, C.POINTER(dbl), vp,
                                              vp, i32]
         L.ucp_grad_ke_electrons.restype = C.c_int
+        L.ucp_set_graphs.argtypes = [vp, i32]
+        L.ucp_set_graphs.restype = C.c_int
         L.ucp_selftest_wait_timeout.argtypes = [vp]
         L.ucp_selftest_wait_timeout.restype = C.c_int
         L.ucp_strerror.argtypes = [i32]
@@ -283,6 +285,9 @@ class Context:
         """Run the bounded-wait self-test; returns the status code (UCP_ETIMEOUT
         means the wait gave up and reported it as it should)."""
         return int(lib().ucp_selftest_wait_timeout(self._h))
+
+    def set_graphs(self, enable=True):
+        self._check(lib().ucp_set_graphs(self._h, int(bool(enable))), "ucp_set_graphs")
 
     def profile(self, enable=True):
         self._check(lib().ucp_profile(self._h, int(bool(enable))), "ucp_profile")

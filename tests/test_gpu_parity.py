@@ -421,3 +421,41 @@ def test_energy_drift_bounded_by_oracle(U, orc):
             g1 = ctx.energy(theta, eps)
         drift = abs(g1[3] - g0[3]) / (g0[0] + g0[1] + abs(g0[2]))
         assert drift <= max(2 * drift_ref, 1e-3), (prec, drift, drift_ref)
+
+
+@pytest.mark.parametrize("prec,k", [(0, 4), (1, 3), (1, 10)])
+def test_graph_blocks_identical(U, prec, k):
+    """Blocks replayed as captured CUDA graphs give bit-identical trajectories
+    (odd k exercises both state-buffer parities)."""
+    c = gaussian_cloud(4096, 1.5, 61)
+    res = []
+    for graphs in (False, True):
+        with _ctx(U, c, 16, prec) as ctx:
+            ctx.set_graphs(graphs)
+            ctx.step(1e-3, k, 2 * k, 0.5, 0.01)
+            ctx.step(1e-3, k, k, 0.5, 0.01)   # replays the captured blocks
+            p, v = ctx.get_state()
+            e = ctx.energy(0.5, 0.01)
+            st = ctx.stats()
+        res.append((p, v, e, st))
+    assert np.array_equal(res[0][0], res[1][0]) and np.array_equal(res[0][1], res[1][1])
+    assert np.array_equal(res[0][2], res[1][2])
+    assert np.array_equal(res[0][3][:4], res[1][3][:4])
+
+
+def test_graph_blocks_batch(U):
+    from paper_0709_3331_gb300.inputs import batched_sizes
+    sizes = [1024, 2048, 512]
+    clouds = [gaussian_cloud(n, 1.0, 90 + i) for i, n in enumerate(sizes)]
+    pos = np.concatenate([x.pos for x in clouds])
+    vel = np.concatenate([x.vel for x in clouds])
+    sp = np.concatenate([x.species for x in clouds])
+    out = []
+    for graphs in (False, True):
+        with U.Context(len(sp), clouds[0].q, clouds[0].m, leaf_cap=8, precision=1,
+                       sizes=sizes) as ctx:
+            ctx.set_state(pos, vel, sp)
+            ctx.set_graphs(graphs)
+            ctx.step(1e-3, 5, 15, 0.5, 0.01)
+            out.append(ctx.get_state())
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
