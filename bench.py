@@ -506,6 +506,28 @@ def run_extras(c, W, ws, pos_d, vel_d, sp_d, Context, UCP_FP32C, UCP_FP64, timed
                 "41 FP32 adjoint walks"}
     ca.close()
 
+    # the small workload (N = 2048, sigma 1, FP64): launch-bound, so each block of
+    # 10 substeps is also run as a captured CUDA graph
+    c0 = gaussian_cloud(2048, 1.0, 1)
+    small = {}
+    for graphs in (False, True):
+        cs0 = Context(c0.n, c0.q, c0.m, leaf_cap=8, precision=UCP_FP64)
+        cs0.set_state(c0.pos, c0.vel, c0.species)
+        cs0.set_graphs(graphs)
+        cs0.step(W["dt_e"], W["k"], 20, 0.5, W["eps"])
+        torch.cuda.synchronize()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        cs0.step(W["dt_e"], W["k"], 100, 0.5, W["eps"])
+        t1.record(stream)
+        torch.cuda.synchronize()
+        ms_s = t0.elapsed_time(t1) / 10
+        small["graphs" if graphs else "streams"] = {
+            "ms_per_block": ms_s, "particle_steps_per_s": c0.n * W["k"] / (ms_s / 1e3)}
+        cs0.close()
+    extra["plain_fp64_n2048"] = small
+
     extra["plain_fp64_n131072"] = {
         "electron_steps": 100, "ms": mp, "particle_steps_per_s": c1.n * 100 / (mp / 1e3),
         "energy_drift": abs(e1[3] - e0[3]) / (e0[0] + e0[1] + abs(e0[2]))}
