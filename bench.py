@@ -229,6 +229,7 @@ def run_gpu(args):
 
     from paper_0709_3331_gb300 import UCP_FP32C, UCP_FP64, Context
     from paper_0709_3331_gb300 import build as B
+    from paper_0709_3331_gb300.ucp import WALK_SHAPE_TABLE
     from paper_0709_3331_gb300.inputs import gaussian_cloud
 
     ws, rank, local = dist_env()
@@ -276,6 +277,9 @@ def run_gpu(args):
     # ---------------- FP32C headline
     ctx = Context(c.n, c.q, c.m, leaf_cap=W["leaf_cap"], precision=UCP_FP32C)
     ctx.set_state(pos_d, vel_d, sp_d)
+    # one-time launch-shape choice of the walk (outside the timed region)
+    shape, shape_ms = ctx.autotune(W["theta"], W["eps"])
+    ctx.stats(reset=True)
     for _ in range(args.warmup):
         ctx.step(W["dt_e"], W["k"], W["k"], W["theta"], W["eps"])
         ctx.energy(W["theta"], W["eps"])
@@ -330,7 +334,10 @@ def run_gpu(args):
                    "eps": W["eps"], "leaf_cap": W["leaf_cap"], "dt_e": W["dt_e"],
                    "ion_substep_ratio": W["k"], "step": "one block of 10 electron substeps",
                    "parallelism": f"replicas x{ws}", "l2": "flushed (256 MB write) before "
-                                                         "every timed step"},
+                                                         "every timed step",
+                   "walk_shape": {"index": shape, "threads": WALK_SHAPE_TABLE[shape][0],
+                                  "blocks_per_sm": WALK_SHAPE_TABLE[shape][1],
+                                  "autotune_ms_per_walk": shape_ms}},
         "particle_steps_per_s": pst,
         "p2p_pairs_per_s": float(st[0]) * ws / (ms_all / 1e3),
         "m2p_evals_per_s": float(st[1]) * ws / (ms_all / 1e3),
@@ -367,6 +374,8 @@ def run_e2e(c, W, args, ws, dev, flush, Context, UCP_FP32C):
     ctx_h = Context(c.n, c.q, c.m, leaf_cap=W["leaf_cap"], precision=UCP_FP32C)
     np_pos, np_vel, np_sp = pin_pos.numpy(), pin_vel.numpy(), pin_sp.numpy()
     np_opos, np_ovel = out_pos.numpy(), out_vel.numpy()
+    ctx_h.set_state(np_pos, np_vel, np_sp)
+    ctx_h.autotune(W["theta"], W["eps"])
     for _ in range(max(1, args.warmup)):
         ctx_h.set_state(np_pos, np_vel, np_sp)
         ctx_h.step(W["dt_e"], W["k"], W["k"], W["theta"], W["eps"])
@@ -443,6 +452,7 @@ def run_extras(c, W, ws, pos_d, vel_d, sp_d, Context, UCP_FP32C, UCP_FP64, timed
     # ensemble of 64 independent clouds (sizes log-uniform 4096..65536, sigma_c =
     # (N_c/2048)^(1/3)) in one context: every stage one launch for all clouds
     from paper_0709_3331_gb300.inputs import batched_sizes, gaussian_cloud
+    from paper_0709_3331_gb300.ucp import WALK_SHAPE_TABLE
     ns, _ = batched_sizes()
     cl = [gaussian_cloud(n, (n / 2048.0) ** (1.0 / 3.0), 4000 + i) for i, n in enumerate(ns)]
     bpos = torch.from_numpy(np.concatenate([x.pos for x in cl])).cuda()
@@ -451,6 +461,7 @@ def run_extras(c, W, ws, pos_d, vel_d, sp_d, Context, UCP_FP32C, UCP_FP64, timed
     ntot = int(sum(ns))
     cb = Context(ntot, c.q, c.m, leaf_cap=W["leaf_cap"], precision=UCP_FP32C, sizes=ns)
     cb.set_state(bpos, bvel, bsp)
+    bshape, _ = cb.autotune(0.5, W["eps"])
     cb.step(W["dt_e"], W["k"], W["k"], 0.5, W["eps"])
     torch.cuda.synchronize()
     msb, stb, wmb, wnb, _ = timed_steps(cb, 2)
@@ -460,6 +471,7 @@ def run_extras(c, W, ws, pos_d, vel_d, sp_d, Context, UCP_FP32C, UCP_FP64, timed
         "particle_steps_per_s": ntot * W["k"] * 2 / (msb / 1e3),
         "walk_frac_fp32_peak": (FLOP_P2P * float(stb[0]) + FLOP_M2P * float(stb[1]))
         / (wmb / 1e3) / 1e12 / peak,
+        "walk_shape": WALK_SHAPE_TABLE[bshape],
         "step": "one block of 10 electron substeps for all 64 clouds, theta 0.5, FP32C"}
     cb.close()
 
@@ -525,6 +537,14 @@ def run_extras(c, W, ws, pos_d, vel_d, sp_d, Context, UCP_FP32C, UCP_FP64, timed
         ms_s = t0.elapsed_time(t1) / 10
         small["graphs" if graphs else "streams"] = {
             "ms_per_block": ms_s, "particle_steps_per_s": c0.n * W["k"] / (ms_s / 1e3)}
+        if not graphs:   # walk time of the same run, from the library's own events
+            cs0.profile(True)
+            cs0.step(W["dt_e"], W["k"], 100, 0.5, W["eps"])
+            torch.cuda.synchronize()
+            wms, wn = cs0.profile_read()
+            cs0.profile(False)
+            small["streams"]["walk_ms_per_block"] = wms / 10
+            small["streams"]["walk_launches_per_block"] = wn / 10
         cs0.close()
     extra["plain_fp64_n2048"] = small
 

@@ -150,6 +150,21 @@ int ucp_grad_ke_electrons(ucp_ctx* ctx, double dt_e, int ion_substep_ratio, int6
  * (small clouds, ensembles). */
 int ucp_set_graphs(ucp_ctx* ctx, int enable);
 
+/* Autotuner of the FP32C walk: times one walk over every particle of the current
+ * state in each launch shape the library has (threads per block x resident blocks
+ * per SM of the persistent walk) and keeps the fastest for this context (returned
+ * in *best_shape, its time in *best_ms; either may be NULL).  Results do not
+ * depend on the shape.  FP64 contexts keep their single shape. */
+int ucp_autotune(ucp_ctx* ctx, double theta, double eps, int* best_shape, float* best_ms);
+
+/* Number of FP32C walk launch shapes, and a call that sets one directly
+ * (0 = the default of 128 threads x 7 blocks per SM; UCP_EINVAL outside
+ * [0, UCP_WALK_SHAPES)).  The trial walks of ucp_autotune overwrite the forces and
+ * interaction counts read by ucp_get_counts, and the next ucp_step recomputes its
+ * first forces. */
+#define UCP_WALK_SHAPES 6
+int ucp_set_walk_shape(ucp_ctx* ctx, int shape);
+
 /* Sec. 5 observables of the current state: out = {KE_ion, KE_electron, PE,
  * E = KE + PE, |P| (total momentum), electron steps taken}.  PE is
  * (1/2) sum_t q_t phi_t with the tree potential; the walk over all particles

@@ -116,7 +116,8 @@ struct WalkArgs {
 };
 void launch_mac_prepare(Tree t, const Cube* cube, double theta, int want_f32, cudaStream_t s);
 void launch_walk_fp64(const WalkArgs& a, int nsm, cudaStream_t s);
-void launch_walk_fp32c(const WalkArgs& a, int nsm, cudaStream_t s);
+void launch_walk_fp32c(const WalkArgs& a, int nsm, cudaStream_t s, int shape);
+int walk_shape_count();
 
 // ---- adjoint (ucp_adjoint.cu) ----
 void launch_walk_adjoint(const WalkArgs& a, const double* lam, double* mu, double* adj, int nn_cap,

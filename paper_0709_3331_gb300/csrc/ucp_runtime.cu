@@ -89,6 +89,7 @@ struct ucp_ctx {
         unsigned long long launches;
     };
     bool use_graphs = false;
+    int walk_shape = 0;                // launch shape of the FP32C walk (ucp_autotune)
     cudaStream_t cap_stream = nullptr;
     std::vector<GraphEntry> graphs;
 
@@ -247,7 +248,7 @@ int force(ucp_ctx* c, double theta, double eps, int electrons_only, bool want_ph
     cudaMemsetAsync(c->cnt_m2p, 0, sizeof(int) * (size_t)c->n, c->s);
     if (a.ntargets > 0) {
         prof_begin(c);
-        if (f32) launch_walk_fp32c(a, c->nsm, c->s);
+        if (f32) launch_walk_fp32c(a, c->nsm, c->s, c->walk_shape);
         else launch_walk_fp64(a, c->nsm, c->s);
         prof_end(c);
         c->walk_targets += a.ntargets;
@@ -757,6 +758,78 @@ static int run_block_graph(ucp_ctx* c, double dt_e, int kk, double theta, double
     c->phi_eps = eps;
     c->walk_launches += kk;
     c->walk_targets += (int64_t)(kk - 1) * c->n_e + c->n;
+    return UCP_OK;
+}
+
+// Times the FP32C walk over every particle of the current state in each launch
+// shape (threads per block x blocks per SM) and keeps the fastest; results do
+// not depend on the shape.
+int ucp_autotune(ucp_ctx* c, double theta, double eps, int* best_shape, float* best_ms)
+{
+    if (!c) return UCP_EINVAL;
+    if (!c->have_state) return fail(c, UCP_ESTATE, "no state");
+    int rc = valid_walk_args(c, theta, eps);
+    if (rc) return rc;
+    if (c->precision != UCP_FP32C) {
+        if (best_shape) *best_shape = 0;
+        return UCP_OK;
+    }
+    if (!c->tree_valid && (rc = build(c))) return rc;
+    const bool prof = c->prof;
+    c->prof = false;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    int best = 0;
+    float best_t = 1e30f;
+    int64_t wt = c->walk_targets, wl = c->walk_launches;
+    unsigned long long st[2];
+    CK(cudaMemcpyAsync(st, c->stats, sizeof(st), cudaMemcpyDeviceToHost, c->s));
+    for (int sh = 0; sh < walk_shape_count() && !rc; ++sh) {
+        c->walk_shape = sh;
+        float tsum = 0.f;
+        for (int rep = 0; rep < 3 && !rc; ++rep) {
+            CK(cudaEventRecord(e0, c->s));
+            rc = force(c, theta, eps, 0, false);
+            CK(cudaEventRecord(e1, c->s));
+            CK(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, e0, e1));
+            if (rep > 0) tsum += ms;   // first run warms caches
+        }
+        if (tsum < best_t) {
+            best_t = tsum;
+            best = sh;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    CK(cudaMemcpyAsync(c->stats, st, sizeof(st), cudaMemcpyHostToDevice, c->s));
+    CK(cudaStreamSynchronize(c->s));
+    c->walk_targets = wt;
+    c->walk_launches = wl;
+    c->walk_shape = best;
+    c->prof = prof;
+    // the trial walks used this call's theta and eps: the next step recomputes
+    // its first forces (identical to the cached ones when theta and eps agree)
+    c->acc_valid = false;
+    for (auto& g : c->graphs) cudaGraphExecDestroy(g.exec);  // recapture with the new shape
+    c->graphs.clear();
+    if (best_shape) *best_shape = best;
+    if (best_ms) *best_ms = best_t / 2.f;
+    return rc;
+}
+
+int ucp_set_walk_shape(ucp_ctx* c, int shape)
+{
+    if (!c) return UCP_EINVAL;
+    if (shape < 0 || shape >= walk_shape_count() || walk_shape_count() != UCP_WALK_SHAPES)
+        return fail(c, UCP_EINVAL, "walk shape out of range");
+    if (c->walk_shape != shape) {
+        for (auto& g : c->graphs) cudaGraphExecDestroy(g.exec);
+        c->graphs.clear();
+    }
+    c->walk_shape = shape;
     return UCP_OK;
 }
 

@@ -107,11 +107,11 @@ __device__ __forceinline__ void m2p<float>(float rx, float ry, float rz, float r
     ez = fmaf(mg3, fmaf(s3, QRz, Dz), fmaf(aa, rz, ez));
 }
 
-template <bool kKelbg>
-__global__ void __launch_bounds__(kWalkThreads)
+template <bool kKelbg, int kThreads>
+__global__ void __launch_bounds__(kThreads)
 k_walk_fp64(WalkArgs a)
 {
-    __shared__ WarpList L[kWalkWarps];
+    __shared__ WarpList L[kThreads / 32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     WarpList& lst = L[w];
     const double q0 = a.qsp[0], q1 = a.qsp[1];
@@ -265,11 +265,13 @@ __device__ __forceinline__ void kelbg_pg(float u, float& p, float& g)
     }
 }
 
-template <bool kKelbg>
-__global__ void __launch_bounds__(kWalkThreads, 7)
+// kThreads threads per block, register budget for 896 resident threads per SM
+// (768 for single-warp blocks, which would spill at the tighter budget)
+template <bool kKelbg, int kThreads>
+__global__ void __launch_bounds__(kThreads, kThreads >= 64 ? 896 / kThreads : 24)
 k_walk_fp32c(WalkArgs a)
 {
-    __shared__ WarpList L[kWalkWarps];
+    __shared__ WarpList L[kThreads / 32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     WarpList& lst = L[w];
     const double q0 = a.qsp[0], q1 = a.qsp[1];
@@ -518,28 +520,68 @@ void launch_mac_prepare(Tree t, const Cube* cube, double theta, int want_f32, cu
     k_mac_prepare<<<blocks, 256, 0, s>>>(t, cube, theta, want_f32);
 }
 
-static int walk_blocks(int nchunks, int nsm, int per_sm)
+static int walk_blocks(int nchunks, int nsm, int per_sm, int warps_per_block)
 {
     int blocks = nsm * per_sm;
-    int need = (nchunks + kWalkWarps - 1) / kWalkWarps;
+    int need = (nchunks + warps_per_block - 1) / warps_per_block;
     if (blocks > need) blocks = need;
     return blocks < 1 ? 1 : blocks;
+}
+
+// Grid of th-thread blocks, per_sm resident per SM.  When the chunks cannot give
+// every SM a block (small clouds), blocks narrow to one warp so the same warps
+// spread over more SMs.  Each warp walks whole chunks, so no shape changes a result.
+static void walk_grid(int nchunks, int nsm, int* th, int per_sm, int* blocks)
+{
+    const int wpb = *th / 32;
+    *blocks = walk_blocks(nchunks, nsm, per_sm, wpb);
+    if (*blocks < nsm && wpb > 1) {
+        *th = 32;
+        *blocks = walk_blocks(nchunks, nsm, per_sm * wpb, 1);
+    }
 }
 
 void launch_walk_fp64(const WalkArgs& a, int nsm, cudaStream_t s)
 {
     count_launch(1);
     cudaMemsetAsync(a.work, 0, sizeof(int), s);
-    if (a.kelbg) k_walk_fp64<true><<<walk_blocks(a.nchunks, nsm, 8), kWalkThreads, 0, s>>>(a);
-    else k_walk_fp64<false><<<walk_blocks(a.nchunks, nsm, 8), kWalkThreads, 0, s>>>(a);
+    int th = kWalkThreads, b;
+    walk_grid(a.nchunks, nsm, &th, 8, &b);
+    if (a.kelbg) {
+        if (th == 32) k_walk_fp64<true, 32><<<b, 32, 0, s>>>(a);
+        else k_walk_fp64<true, kWalkThreads><<<b, kWalkThreads, 0, s>>>(a);
+    } else {
+        if (th == 32) k_walk_fp64<false, 32><<<b, 32, 0, s>>>(a);
+        else k_walk_fp64<false, kWalkThreads><<<b, kWalkThreads, 0, s>>>(a);
+    }
 }
 
-void launch_walk_fp32c(const WalkArgs& a, int nsm, cudaStream_t s)
+// Launch shapes of the FP32C walk that the autotuner chooses from: threads per
+// block and blocks per SM (the persistent grid takes 32-target chunks from a
+// counter, so the shape changes the schedule, never a result).
+static const int kShapes[][2] = {{128, 7}, {64, 14}, {256, 3}, {128, 14}, {64, 28}, {256, 6}};
+int walk_shape_count() { return (int)(sizeof(kShapes) / sizeof(kShapes[0])); }
+
+template <bool kKelbg>
+static void walk_fp32c_shape(const WalkArgs& a, int th, int b, cudaStream_t s)
+{
+    switch (th) {
+    case 32: k_walk_fp32c<kKelbg, 32><<<b, 32, 0, s>>>(a); break;
+    case 64: k_walk_fp32c<kKelbg, 64><<<b, 64, 0, s>>>(a); break;
+    case 256: k_walk_fp32c<kKelbg, 256><<<b, 256, 0, s>>>(a); break;
+    default: k_walk_fp32c<kKelbg, 128><<<b, 128, 0, s>>>(a); break;
+    }
+}
+
+void launch_walk_fp32c(const WalkArgs& a, int nsm, cudaStream_t s, int shape)
 {
     count_launch(1);
     cudaMemsetAsync(a.work, 0, sizeof(int), s);
-    if (a.kelbg) k_walk_fp32c<true><<<walk_blocks(a.nchunks, nsm, 12), kWalkThreads, 0, s>>>(a);
-    else k_walk_fp32c<false><<<walk_blocks(a.nchunks, nsm, 12), kWalkThreads, 0, s>>>(a);
+    if (shape < 0 || shape >= walk_shape_count()) shape = 0;
+    int th = kShapes[shape][0], b;
+    walk_grid(a.nchunks, nsm, &th, kShapes[shape][1], &b);
+    if (a.kelbg) walk_fp32c_shape<true>(a, th, b, s);
+    else walk_fp32c_shape<false>(a, th, b, s);
 }
 
 }  // namespace ucp

@@ -20,12 +20,16 @@ UCP_OK, UCP_EINVAL, UCP_ENOMEM, UCP_ECUDA, UCP_ENONFINITE, UCP_ETIMEOUT, UCP_EST
 UCP_FP64, UCP_FP32C = 0, 1
 UCP_ION, UCP_ELECTRON = 0, 1
 UCP_POT_PLUMMER, UCP_POT_KELBG = 0, 1
+UCP_WALK_SHAPES = 6
+# (threads per block, blocks per SM) of each FP32C walk launch shape
+WALK_SHAPE_TABLE = ((128, 7), (64, 14), (256, 3), (128, 14), (64, 28), (256, 6))
 
 EXPORTS = ("ucp_create", "ucp_destroy", "ucp_set_state", "ucp_get_state", "ucp_tree_build",
            "ucp_tree_force", "ucp_step", "ucp_energy", "ucp_stats", "ucp_get_cube",
            "ucp_get_sorted", "ucp_get_tree", "ucp_get_counts", "ucp_profile", "ucp_profile_read",
            "ucp_strerror", "ucp_last_error", "ucp_selftest_wait_timeout", "ucp_create_batch",
-           "ucp_energy_clouds", "ucp_get_cubes", "ucp_grad_ke_electrons", "ucp_set_graphs")
+           "ucp_energy_clouds", "ucp_get_cubes", "ucp_grad_ke_electrons", "ucp_set_graphs",
+           "ucp_autotune", "ucp_set_walk_shape")
 
 
 class UcpError(RuntimeError):
@@ -76,6 +80,10 @@ def lib():
         L.ucp_grad_ke_electrons.argtypes = [vp, dbl, i32, i64, dbl, dbl, i64, C.POINTER(dbl), vp,
                                              vp, i32]
         L.ucp_grad_ke_electrons.restype = C.c_int
+        L.ucp_autotune.argtypes = [vp, dbl, dbl, C.POINTER(i32), C.POINTER(C.c_float)]
+        L.ucp_autotune.restype = C.c_int
+        L.ucp_set_walk_shape.argtypes = [vp, i32]
+        L.ucp_set_walk_shape.restype = C.c_int
         L.ucp_set_graphs.argtypes = [vp, i32]
         L.ucp_set_graphs.restype = C.c_int
         L.ucp_selftest_wait_timeout.argtypes = [vp]
@@ -285,6 +293,19 @@ class Context:
         """Run the bounded-wait self-test; returns the status code (UCP_ETIMEOUT
         means the wait gave up and reported it as it should)."""
         return int(lib().ucp_selftest_wait_timeout(self._h))
+
+    def autotune(self, theta, eps):
+        """Pick the fastest launch shape of the FP32C walk on the current state;
+        returns (shape index, ms per walk)."""
+        sh = C.c_int(0)
+        ms = C.c_float(0.0)
+        self._check(lib().ucp_autotune(self._h, float(theta), float(eps), C.byref(sh),
+                                       C.byref(ms)), "ucp_autotune")
+        return sh.value, ms.value
+
+    def set_walk_shape(self, shape):
+        """Set the FP32C walk launch shape (0 .. WALK_SHAPES-1) directly."""
+        self._check(lib().ucp_set_walk_shape(self._h, int(shape)), "ucp_set_walk_shape")
 
     def set_graphs(self, enable=True):
         self._check(lib().ucp_set_graphs(self._h, int(bool(enable))), "ucp_set_graphs")

@@ -77,3 +77,19 @@ def test_product_does_not_import_the_oracle():
         if f.endswith((".py", ".cu", ".cuh", ".h")):
             src = open(f).read()
             assert not re.search(r"(from|import)\s+oracle|liboracle|ucp_oracle", src), f
+
+
+def test_walk_shape_count_matches_header():
+    from paper_0709_3331_gb300 import ucp
+    src = open(os.path.join(ROOT, "include", "ucp.h")).read()
+    m = re.search(r"#define UCP_WALK_SHAPES (\d+)", src)
+    assert m and int(m.group(1)) == ucp.UCP_WALK_SHAPES
+    cu = open(os.path.join(ROOT, "paper_0709_3331_gb300", "csrc", "ucp_walk.cu")).read()
+    tab = re.search(r"kShapes\[\]\[2\] = \{(.*?)\};", cu).group(1)
+    pairs = tuple((int(a), int(b)) for a, b in re.findall(r"\{(\d+), (\d+)\}", tab))
+    assert pairs == ucp.WALK_SHAPE_TABLE and len(pairs) == ucp.UCP_WALK_SHAPES
+
+
+def test_walk_shape_rejects_null_context(L):
+    L.ucp_set_walk_shape.argtypes = [C.c_void_p, C.c_int]
+    assert L.ucp_set_walk_shape(None, 0) == -1
