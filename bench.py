@@ -306,11 +306,16 @@ def run_gpu(args):
     peak_mhz = 2070.0
     peak = sm_peak_tflops(nsm, peak_mhz)
     traffic = traffic_record()
+    from paper_0709_3331_gb300.ucp import measure_peaks
+    mpk = measure_peaks(stream.cuda_stream)
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": (achieved / peak) if achieved else None,
                 "traffic": traffic, "kernel": "k_walk_fp32c",
                 "peak_basis": f"FP32 pipe: {nsm} SMs x 128 lanes x 2 flop x {peak_mhz:.0f} MHz "
                               "(max SM clock); flops = 20 per direct pair + 64 per multipole",
+                "measured_peaks": mpk,
+                "frac_of_measured_fp32_fma": (achieved / mpk["fp32_fma_tflops"]) if achieved
+                else None,
                 "walk_ms_per_launch": walk_ms / max(walk_n, 1), "walk_launches": walk_n,
                 "walk_share_of_step": walk_ms / ms if ms > 0 else None}
 

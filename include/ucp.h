@@ -215,6 +215,15 @@ int ucp_profile_read(ucp_ctx* ctx, double* walk_ms, int64_t* walk_launches);
 const char* ucp_strerror(int code);
 const char* ucp_last_error(ucp_ctx* ctx);
 
+/* Throughput of the arithmetic units the tree walk is bound by, measured on the
+ * current device (no counterpart in the paper; it gives the walk's roofline a
+ * denominator measured at the clocks of the run).  out = {FP32 FMA TFLOP/s,
+ * packed FP32x2 FMA TFLOP/s, reciprocal square roots per second / 1e9, FP64
+ * FMA TFLOP/s} (an FMA counts as 2 flops).  Runs about 0.1 s of kernels on
+ * stream and synchronises it; allocates and frees a small scratch buffer.
+ * UCP_EINVAL for out == NULL, UCP_ENOMEM, UCP_ECUDA. */
+int ucp_measure_peaks(double out[4], void* stream);
+
 /* Enclosing cube without any allocation.  The paper has no counterpart: this
  * is a service for callers that must not allocate GPU memory at this point --
  * for example code running while a CUDA graph is being captured (where

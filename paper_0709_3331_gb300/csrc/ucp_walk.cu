@@ -544,9 +544,9 @@ static void walk_grid(int nchunks, int nsm, int* th, int per_sm, int* blocks)
 void launch_walk_fp64(const WalkArgs& a, int nsm, cudaStream_t s)
 {
     count_launch(1);
-    cudaMemsetAsync(a.work, 0, sizeof(int), s);
     int th = kWalkThreads, b;
     walk_grid(a.nchunks, nsm, &th, 8, &b);
+    cudaMemsetAsync(a.work, 0, sizeof(int), s);
     if (a.kelbg) {
         if (th == 32) k_walk_fp64<true, 32><<<b, 32, 0, s>>>(a);
         else k_walk_fp64<true, kWalkThreads><<<b, kWalkThreads, 0, s>>>(a);
@@ -559,7 +559,7 @@ void launch_walk_fp64(const WalkArgs& a, int nsm, cudaStream_t s)
 // Launch shapes of the FP32C walk that the autotuner chooses from: threads per
 // block and blocks per SM (the persistent grid takes 32-target chunks from a
 // counter, so the shape changes the schedule, never a result).
-static const int kShapes[][2] = {{128, 7}, {64, 14}, {256, 3}, {128, 14}, {64, 28}, {256, 6}};
+static const int kShapes[][2] = {{128, 7}, {64, 14}, {256, 3}, {896, 1}, {448, 2}, {224, 4}};
 int walk_shape_count() { return (int)(sizeof(kShapes) / sizeof(kShapes[0])); }
 
 template <bool kKelbg>
@@ -568,7 +568,10 @@ static void walk_fp32c_shape(const WalkArgs& a, int th, int b, cudaStream_t s)
     switch (th) {
     case 32: k_walk_fp32c<kKelbg, 32><<<b, 32, 0, s>>>(a); break;
     case 64: k_walk_fp32c<kKelbg, 64><<<b, 64, 0, s>>>(a); break;
+    case 224: k_walk_fp32c<kKelbg, 224><<<b, 224, 0, s>>>(a); break;
     case 256: k_walk_fp32c<kKelbg, 256><<<b, 256, 0, s>>>(a); break;
+    case 448: k_walk_fp32c<kKelbg, 448><<<b, 448, 0, s>>>(a); break;
+    case 896: k_walk_fp32c<kKelbg, 896><<<b, 896, 0, s>>>(a); break;
     default: k_walk_fp32c<kKelbg, 128><<<b, 128, 0, s>>>(a); break;
     }
 }
@@ -576,10 +579,10 @@ static void walk_fp32c_shape(const WalkArgs& a, int th, int b, cudaStream_t s)
 void launch_walk_fp32c(const WalkArgs& a, int nsm, cudaStream_t s, int shape)
 {
     count_launch(1);
-    cudaMemsetAsync(a.work, 0, sizeof(int), s);
     if (shape < 0 || shape >= walk_shape_count()) shape = 0;
     int th = kShapes[shape][0], b;
     walk_grid(a.nchunks, nsm, &th, kShapes[shape][1], &b);
+    cudaMemsetAsync(a.work, 0, sizeof(int), s);
     if (a.kelbg) walk_fp32c_shape<true>(a, th, b, s);
     else walk_fp32c_shape<false>(a, th, b, s);
 }

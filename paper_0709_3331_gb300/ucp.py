@@ -22,14 +22,14 @@ UCP_ION, UCP_ELECTRON = 0, 1
 UCP_POT_PLUMMER, UCP_POT_KELBG = 0, 1
 UCP_WALK_SHAPES = 6
 # (threads per block, blocks per SM) of each FP32C walk launch shape
-WALK_SHAPE_TABLE = ((128, 7), (64, 14), (256, 3), (128, 14), (64, 28), (256, 6))
+WALK_SHAPE_TABLE = ((128, 7), (64, 14), (256, 3), (896, 1), (448, 2), (224, 4))
 
 EXPORTS = ("ucp_create", "ucp_destroy", "ucp_set_state", "ucp_get_state", "ucp_tree_build",
            "ucp_tree_force", "ucp_step", "ucp_energy", "ucp_stats", "ucp_get_cube",
            "ucp_get_sorted", "ucp_get_tree", "ucp_get_counts", "ucp_profile", "ucp_profile_read",
            "ucp_strerror", "ucp_last_error", "ucp_selftest_wait_timeout", "ucp_create_batch",
            "ucp_energy_clouds", "ucp_get_cubes", "ucp_grad_ke_electrons", "ucp_set_graphs",
-           "ucp_autotune", "ucp_set_walk_shape")
+           "ucp_autotune", "ucp_set_walk_shape", "ucp_measure_peaks")
 
 
 class UcpError(RuntimeError):
@@ -82,6 +82,8 @@ def lib():
         L.ucp_grad_ke_electrons.restype = C.c_int
         L.ucp_autotune.argtypes = [vp, dbl, dbl, C.POINTER(i32), C.POINTER(C.c_float)]
         L.ucp_autotune.restype = C.c_int
+        L.ucp_measure_peaks.argtypes = [C.POINTER(C.c_double), vp]
+        L.ucp_measure_peaks.restype = C.c_int
         L.ucp_set_walk_shape.argtypes = [vp, i32]
         L.ucp_set_walk_shape.restype = C.c_int
         L.ucp_set_graphs.argtypes = [vp, i32]
@@ -99,6 +101,20 @@ def lib():
             getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
+
+
+def measure_peaks(stream=None):
+    """Measured arithmetic throughput of the current device:
+    {"fp32_fma_tflops", "fp32x2_fma_tflops", "rsqrt_gops", "fp64_fma_tflops"}."""
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream().cuda_stream
+    out = (C.c_double * 4)()
+    rc = lib().ucp_measure_peaks(out, stream)
+    if rc:
+        raise UcpError(rc, "ucp_measure_peaks")
+    return {"fp32_fma_tflops": out[0], "fp32x2_fma_tflops": out[1], "rsqrt_gops": out[2],
+            "fp64_fma_tflops": out[3]}
 
 
 def _is_torch(a):

@@ -1,0 +1,107 @@
+"""Parity at full size: N = 524,288 (sigma 8, leaf_cap 16, eps 0.01, dt_e 1e-3,
+k = 10), the precision workload the benchmark times, in the walk launch shape
+the autotuner picks for it.  The oracle computes sampled targets one by one on
+the GPU's own state, at electron steps 0, 50 and 100 of the split-step run, and
+the opening angles 0.3, 0.5 and 0.7 at step 0; the direct sum on a smaller
+sample checks that the GPU's tree error is the oracle's tree error."""
+import math
+import os
+
+import numpy as np
+import pytest
+
+from paper_0709_3331_gb300.inputs import workload
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-5
+FP32C_TOL = 1e-4
+NTHREADS = max(1, min(16, os.cpu_count() or 1))
+
+
+@pytest.fixture(scope="module")
+def U():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_0709_3331_gb300 import build as b
+    b.build()
+    import paper_0709_3331_gb300 as P
+    return P
+
+
+@pytest.fixture(scope="module")
+def cloud():
+    c = workload("precision_n524288")
+    assert c.n == 524288
+    return c
+
+
+def rel_rms(a, b):
+    return math.sqrt(((a - b) ** 2).sum() / (b ** 2).sum())
+
+
+def _sample(n, k, seed):
+    return np.sort(np.random.default_rng(seed).choice(n, k, replace=False))
+
+
+def _oracle(orc, pos, c, theta, tl):
+    T = orc.Tree(pos, c.species, c.q, leaf_cap=16)
+    E, phi, npp, nmp = T.force(theta, 0.01, targets=tl, nthreads=NTHREADS, counts=True)
+    qm = (c.q[c.species[tl]] / c.m[c.species[tl]])[:, None]
+    return E * qm, phi, npp, nmp
+
+
+def test_fullsize_fp32c_steps_0_50_100(U, orc, cloud):
+    c = cloud
+    tl = _sample(c.n, 4096, 50)
+    with U.Context(c.n, c.q, c.m, leaf_cap=16, precision=U.UCP_FP32C) as ctx:
+        ctx.set_state(c.pos, c.vel, c.species)
+        ctx.autotune(0.5, 0.01)
+        for step in (0, 50, 100):
+            if step:
+                ctx.step(1e-3, 10, 50, 0.5, 0.01)
+            pos, _ = ctx.get_state()
+            assert np.isfinite(pos).all()
+            acc, phi = ctx.tree_force(0.5, 0.01)
+            gp, gm = ctx.get_counts()
+            a_ref, p_ref, npp, nmp = _oracle(orc, pos, c, 0.5, tl)
+            assert rel_rms(acc[tl], a_ref) <= FP32C_TOL, step
+            assert rel_rms(phi[tl], p_ref) <= FP32C_TOL, step
+            mism = np.count_nonzero((gp[tl] != npp) | (gm[tl] != nmp))
+            assert mism <= 2 + tl.size // 1000, (step, mism)
+
+
+@pytest.mark.parametrize("prec,theta", [(0, 0.3), (0, 0.5), (0, 0.7), (1, 0.3), (1, 0.7)])
+def test_fullsize_theta(U, orc, cloud, prec, theta):
+    c = cloud
+    tl = _sample(c.n, 2048, 7)
+    with U.Context(c.n, c.q, c.m, leaf_cap=16, precision=prec) as ctx:
+        ctx.set_state(c.pos, c.vel, c.species)
+        if prec == U.UCP_FP32C:
+            ctx.autotune(theta, 0.01)
+        acc, phi = ctx.tree_force(theta, 0.01)
+        gp, gm = ctx.get_counts()
+    a_ref, p_ref, npp, nmp = _oracle(orc, c.pos, c, theta, tl)
+    tol = FP64_TOL if prec == U.UCP_FP64 else FP32C_TOL
+    assert rel_rms(acc[tl], a_ref) <= tol
+    assert rel_rms(phi[tl], p_ref) <= tol
+    mism = np.count_nonzero((gp[tl] != npp) | (gm[tl] != nmp))
+    assert mism <= 2 + tl.size // 1000, mism
+
+
+def test_fullsize_tree_error_vs_direct(U, orc, cloud):
+    c = cloud
+    tl = _sample(c.n, 512, 99)
+    with U.Context(c.n, c.q, c.m, leaf_cap=16, precision=U.UCP_FP32C) as ctx:
+        ctx.set_state(c.pos, c.vel, c.species)
+        acc, _ = ctx.tree_force(0.5, 0.01)
+    E, _ = orc.direct(c.pos, c.species, c.q, 0.01, targets=tl, nthreads=NTHREADS)
+    a_dir = E * (c.q[c.species[tl]] / c.m[c.species[tl]])[:, None]
+    a_tree, _, _, _ = _oracle(orc, c.pos, c, 0.5, tl)
+    err_gpu = rel_rms(acc[tl], a_dir)
+    err_orc = rel_rms(a_tree, a_dir)
+    # the expansion error at theta 0.5 is well below a percent, and the GPU's
+    # error differs from the oracle's only by its FP32 rounding
+    assert err_orc < 1e-2
+    assert abs(err_gpu - err_orc) <= FP32C_TOL
