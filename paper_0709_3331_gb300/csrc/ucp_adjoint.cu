@@ -307,9 +307,9 @@ k_walk_adjoint_f32(WalkArgs a, const double* __restrict__ lam, double* __restric
                 const bool in = (lst.mask[e] >> lane) & 1u;
                 const float4* r = F + (size_t)nd * kF32;
                 const float4 A = r[0], B = r[1], C = r[2];
-                const float rx = (xh - A.x) + (xl - B.x), ry = (yh - A.y) + (yl - B.y),
-                            rz = (zh - A.z) + (zl - B.z);
-                const int jb = __float_as_int(C.x), je = __float_as_int(C.y);
+                const float rx = (xh + A.x) + (xl + B.x), ry = (yh + A.y) + (yl + B.y),
+                            rz = (zh + A.z) + (zl + B.z);
+                const int jb = __ldg(&a.t.info[nd].x), je = __float_as_int(C.y);
                 for (int j = jb; j < je; ++j) {
                     const float4 P = __ldg(S + (j & ~1)), Q = __ldg(S + (j & ~1) + 1);
                     const bool odd = j & 1;
@@ -350,8 +350,8 @@ k_walk_adjoint_f32(WalkArgs a, const double* __restrict__ lam, double* __restric
             const int nxt = __float_as_int(B.w);
             const bool leaf = __float_as_int(C.y) >= 0;
             const bool active = node >= skip;
-            const float R[3] = {(xh - A.x) + (xl - B.x), (yh - A.y) + (yl - B.y),
-                                (zh - A.z) + (zl - B.z)};
+            const float R[3] = {(xh + A.x) + (xl + B.x), (yh + A.y) + (yl + B.y),
+                                (zh + A.z) + (zl + B.z)};
             const float d2 = dot3f(R, R);
             bool acc = active && (A.w < d2);
             if (active && fabsf(d2 - A.w) <= 4e-6f * d2) {

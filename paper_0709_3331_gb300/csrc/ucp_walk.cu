@@ -83,11 +83,11 @@ __device__ __forceinline__ void m2p<double>(double rx, double ry, double rz, dou
     ez += aa * rz - g3 * (Dz + s3 * QRz);
 }
 
-template <>
-__device__ __forceinline__ void m2p<float>(float rx, float ry, float rz, float r2, float M, float Dx,
-                                           float Dy, float Dz, float Qxx, float Qxy, float Qxz,
-                                           float Qyy, float Qyz, float Qzz, float& ex, float& ey,
-                                           float& ez, float& ph)
+// FP32 form; T = -tr(Q)/2 comes with the box record
+__device__ __forceinline__ void m2p_f32(float rx, float ry, float rz, float r2, float T, float M,
+                                        float Dx, float Dy, float Dz, float Qxx, float Qxy,
+                                        float Qxz, float Qyy, float Qyz, float Qzz, float& ex,
+                                        float& ey, float& ez, float& ph)
 {
     float g = rsqrtf(r2);
     float u = g * g;
@@ -96,7 +96,7 @@ __device__ __forceinline__ void m2p<float>(float rx, float ry, float rz, float r
     float QRy = fmaf(Qxy, rx, fmaf(Qyy, ry, Qyz * rz));
     float QRz = fmaf(Qxz, rx, fmaf(Qyz, ry, Qzz * rz));
     float RQR = fmaf(rx, QRx, fmaf(ry, QRy, rz * QRz));
-    float w = fmaf(Dx, rx, fmaf(Dy, ry, fmaf(Dz, rz, -0.5f * (Qxx + Qyy + Qzz))));
+    float w = fmaf(Dx, rx, fmaf(Dy, ry, fmaf(Dz, rz, T)));
     float h = u * RQR;
     ph = fmaf(g, fmaf(u, fmaf(1.5f, h, w), M), ph);
     float s3 = 3.f * u;
@@ -288,13 +288,15 @@ k_walk_fp32c(WalkArgs a)
         const int t = valid ? (a.targets ? a.targets[ti] : ti) : -1;
         const int root = a.pos_off[a.t.cloud_start ? a.t.cloud_start[ck.z] : 0];
         const int end = __float_as_int(F[(size_t)root * kF32 + 1].w);
-        // target as an unevaluated float pair: x = xh + xl
+        // target as an unevaluated float pair: x = xh + xl ({x, y} packed for the
+        // FP32x2 adds)
         float xh = 0.f, yh = 0.f, zh = 0.f, xl = 0.f, yl = 0.f, zl = 0.f;
         if (valid) {
             double X = a.x[t], Y = a.y[t], Z = a.z[t];
             xh = (float)X; yh = (float)Y; zh = (float)Z;
             xl = (float)(X - (double)xh); yl = (float)(Y - (double)yh); zl = (float)(Z - (double)zh);
         }
+        const float2 xyh = make_float2(xh, yh), xyl = make_float2(xl, yl);
         const float qt = valid ? (a.sp[t] ? (float)q1 : (float)q0) : 0.f;
         const float inv_lambda = (float)(1.0 / a.lambda);
         const float inv_lambda3 = inv_lambda * inv_lambda * inv_lambda;
@@ -320,10 +322,10 @@ k_walk_fp32c(WalkArgs a)
                 if ((lst.mask[e] >> lane) & 1u) {
                     const float4* r = F + (size_t)nd * kF32;
                     float4 A = r[0], B = r[1], C = r[2];
-                    float rx = (xh - A.x) + (xl - B.x);
-                    float ry = (yh - A.y) + (yl - B.y);
-                    float rz = (zh - A.z) + (zl - B.z);
-                    int jb = __float_as_int(C.x), je = __float_as_int(C.y);
+                    float rx = (xh + A.x) + (xl + B.x);
+                    float ry = (yh + A.y) + (yl + B.y);
+                    float rz = (zh + A.z) + (zl + B.z);
+                    int jb = __ldg(&a.t.info[nd].x), je = __float_as_int(C.y);
                     if (kKelbg) {
                         // one source at a time: unlike charges (electron-ion) take the
                         // Kelbg form, like charges the softened Coulomb law
@@ -409,15 +411,17 @@ k_walk_fp32c(WalkArgs a)
             const int nxt = __float_as_int(B.w);
             const bool leaf = __float_as_int(C.y) >= 0;
             const bool active = node >= skip;
-            float rx = (xh - A.x) + (xl - B.x);
-            float ry = (yh - A.y) + (yl - B.y);
-            float rz = (zh - A.z) + (zl - B.z);
+            const float2 rxy = __fadd2_rn(__fadd2_rn(xyh, make_float2(A.x, A.y)),
+                                          __fadd2_rn(xyl, make_float2(B.x, B.y)));
+            const float rx = rxy.x, ry = rxy.y;
+            const float rz = (zh + A.z) + (zl + B.z);
             float d2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
-            bool acc = active && (A.w < d2);
+            const float dm = d2 - A.w;
+            bool acc = active && dm > 0.f;
             // Within FP32 rounding of the threshold the decision is taken again in
             // FP64 exactly as the FP64 walk takes it, so both precisions open the
             // same boxes (rare: |d2 - rcrit2| <= 4e-6 d2).
-            if (active && fabsf(d2 - A.w) <= 4e-6f * d2) {
+            if (active && fabsf(dm) <= 4e-6f * d2) {
                 const double* m = a.t.mom + (size_t)node * kMom;
                 double dx = __dsub_rn(a.x[t], m[0]);
                 double dy = __dsub_rn(a.y[t], m[1]);
@@ -442,8 +446,8 @@ k_walk_fp32c(WalkArgs a)
                 }
             }
             if (acc) {
-                m2p<float>(rx, ry, rz, d2 + eps2, C.z, C.w, D.x, D.y, D.z, D.w, E.x, E.y, E.z,
-                           E.w, bx, by, bz, bp);
+                m2p_f32(rx, ry, rz, d2 + eps2, C.x, C.z, C.w, D.x, D.y, D.z, D.w, E.x, E.y, E.z,
+                        E.w, bx, by, bz, bp);
                 ++nm;
             }
             if ((++vis & (kM2PBatch - 1)) == 0) fold_batch();
@@ -497,11 +501,14 @@ __global__ void k_mac_prepare(Tree t, const Cube* __restrict__ cube, double thet
         if (want_f32) {
             int4 inf = t.info[nd];
             float4* r = t.f32 + (size_t)nd * kF32;
+            // the centroid enters negated (x_t - c as a sum), the trace term of
+            // the expansion as one value
             float chx = (float)m[0], chy = (float)m[1], chz = (float)m[2];
-            r[0] = make_float4(chx, chy, chz, (float)r2);
-            r[1] = make_float4((float)(m[0] - (double)chx), (float)(m[1] - (double)chy),
-                               (float)(m[2] - (double)chz), __int_as_float(inf.z));
-            r[2] = make_float4(__int_as_float((dl & 256) ? inf.x : 0),
+            r[0] = make_float4(-chx, -chy, -chz, (float)r2);
+            r[1] = make_float4((float)((double)chx - m[0]), (float)((double)chy - m[1]),
+                               (float)((double)chz - m[2]), __int_as_float(inf.z));
+            const float qxx = (float)m[MQ], qyy = (float)m[MQ + 3], qzz = (float)m[MQ + 5];
+            r[2] = make_float4(-0.5f * ((qxx + qyy) + qzz),
                                __int_as_float((dl & 256) ? inf.y : -1), (float)m[MM],
                                (float)m[MD]);
             r[3] = make_float4((float)m[MD + 1], (float)m[MD + 2], (float)m[MQ], (float)m[MQ + 1]);
