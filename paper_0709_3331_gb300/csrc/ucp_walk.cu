@@ -265,10 +265,9 @@ __device__ __forceinline__ void kelbg_pg(float u, float& p, float& g)
     }
 }
 
-// kThreads threads per block, register budget for 896 resident threads per SM
-// (768 for single-warp blocks, which would spill at the tighter budget)
-template <bool kKelbg, int kThreads>
-__global__ void __launch_bounds__(kThreads, kThreads >= 64 ? 896 / kThreads : 24)
+// kThreads threads per block, register budget for kBlocks resident blocks per SM
+template <bool kKelbg, int kThreads, int kBlocks>
+__global__ void __launch_bounds__(kThreads, kBlocks)
 k_walk_fp32c(WalkArgs a)
 {
     __shared__ WarpList L[kThreads / 32];
@@ -564,34 +563,34 @@ void launch_walk_fp64(const WalkArgs& a, int nsm, cudaStream_t s)
 }
 
 // Launch shapes of the FP32C walk that the autotuner chooses from: threads per
-// block and blocks per SM (the persistent grid takes 32-target chunks from a
-// counter, so the shape changes the schedule, never a result).
-static const int kShapes[][2] = {{128, 7}, {64, 14}, {256, 3}, {896, 1}, {448, 2}, {224, 4}};
+// block and resident blocks per SM, which also sets the register budget (28
+// warps per SM at 72 registers, 32 at 64).  The persistent grid takes 32-target
+// chunks from a counter, so the shape changes the schedule, never a result.
+static const int kShapes[][2] = {{128, 7}, {896, 1}, {128, 8}, {1024, 1}, {256, 4}, {512, 2}};
 int walk_shape_count() { return (int)(sizeof(kShapes) / sizeof(kShapes[0])); }
 
 template <bool kKelbg>
-static void walk_fp32c_shape(const WalkArgs& a, int th, int b, cudaStream_t s)
+static void walk_fp32c_shape(const WalkArgs& a, int th, int per_sm, int b, cudaStream_t s)
 {
-    switch (th) {
-    case 32: k_walk_fp32c<kKelbg, 32><<<b, 32, 0, s>>>(a); break;
-    case 64: k_walk_fp32c<kKelbg, 64><<<b, 64, 0, s>>>(a); break;
-    case 224: k_walk_fp32c<kKelbg, 224><<<b, 224, 0, s>>>(a); break;
-    case 256: k_walk_fp32c<kKelbg, 256><<<b, 256, 0, s>>>(a); break;
-    case 448: k_walk_fp32c<kKelbg, 448><<<b, 448, 0, s>>>(a); break;
-    case 896: k_walk_fp32c<kKelbg, 896><<<b, 896, 0, s>>>(a); break;
-    default: k_walk_fp32c<kKelbg, 128><<<b, 128, 0, s>>>(a); break;
-    }
+    if (th == 32) k_walk_fp32c<kKelbg, 32, 24><<<b, 32, 0, s>>>(a);
+    else if (th == 896) k_walk_fp32c<kKelbg, 896, 1><<<b, 896, 0, s>>>(a);
+    else if (th == 1024) k_walk_fp32c<kKelbg, 1024, 1><<<b, 1024, 0, s>>>(a);
+    else if (th == 256) k_walk_fp32c<kKelbg, 256, 4><<<b, 256, 0, s>>>(a);
+    else if (th == 512) k_walk_fp32c<kKelbg, 512, 2><<<b, 512, 0, s>>>(a);
+    else if (per_sm >= 8) k_walk_fp32c<kKelbg, 128, 8><<<b, 128, 0, s>>>(a);
+    else k_walk_fp32c<kKelbg, 128, 7><<<b, 128, 0, s>>>(a);
 }
 
 void launch_walk_fp32c(const WalkArgs& a, int nsm, cudaStream_t s, int shape)
 {
     count_launch(1);
+    cudaMemsetAsync(a.work, 0, sizeof(int), s);
     if (shape < 0 || shape >= walk_shape_count()) shape = 0;
     int th = kShapes[shape][0], b;
-    walk_grid(a.nchunks, nsm, &th, kShapes[shape][1], &b);
-    cudaMemsetAsync(a.work, 0, sizeof(int), s);
-    if (a.kelbg) walk_fp32c_shape<true>(a, th, b, s);
-    else walk_fp32c_shape<false>(a, th, b, s);
+    const int per_sm = kShapes[shape][1];
+    walk_grid(a.nchunks, nsm, &th, per_sm, &b);
+    if (a.kelbg) walk_fp32c_shape<true>(a, th, per_sm, b, s);
+    else walk_fp32c_shape<false>(a, th, per_sm, b, s);
 }
 
 }  // namespace ucp

@@ -22,7 +22,7 @@ UCP_ION, UCP_ELECTRON = 0, 1
 UCP_POT_PLUMMER, UCP_POT_KELBG = 0, 1
 UCP_WALK_SHAPES = 6
 # (threads per block, blocks per SM) of each FP32C walk launch shape
-WALK_SHAPE_TABLE = ((128, 7), (64, 14), (256, 3), (896, 1), (448, 2), (224, 4))
+WALK_SHAPE_TABLE = ((128, 7), (896, 1), (128, 8), (1024, 1), (256, 4), (512, 2))
 
 EXPORTS = ("ucp_create", "ucp_destroy", "ucp_set_state", "ucp_get_state", "ucp_tree_build",
            "ucp_tree_force", "ucp_step", "ucp_energy", "ucp_stats", "ucp_get_cube",
