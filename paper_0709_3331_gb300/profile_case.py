@@ -24,6 +24,7 @@ def main():
     ap.add_argument("--leaf-cap", type=int, default=16)
     ap.add_argument("--what", default="force", choices=["force", "step"])
     ap.add_argument("--repeat", type=int, default=1)
+    ap.add_argument("--shape", type=int, default=0, help="FP32C walk launch shape")
     a = ap.parse_args()
     w = dict(WORKLOADS[a.workload])
     if a.n:
@@ -34,6 +35,8 @@ def main():
     ctx = Context(c.n, c.q, c.m, leaf_cap=a.leaf_cap, precision=prec)
     ctx.set_state(torch.from_numpy(c.pos).to(dev), torch.from_numpy(c.vel).to(dev),
                   torch.from_numpy(c.species).to(dev))
+    if prec == UCP_FP32C:
+        ctx.set_walk_shape(a.shape)
     acc = torch.empty((c.n, 3), dtype=torch.float64, device=dev)
     phi = torch.empty(c.n, dtype=torch.float64, device=dev)
     for _ in range(a.repeat):
