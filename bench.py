@@ -68,6 +68,7 @@ class Clocks:
         self.index = index
         self.proc = None
         self.path = None
+        self.skip = 0
 
     def start(self):
         try:
@@ -75,10 +76,18 @@ class Clocks:
             os.close(fd)
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "100"],
                 stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
+            return
+        # the timed region starts once the sampler is producing rows (at most 3 s)
+        t0 = time.time()
+        while time.time() - t0 < 3.0 and self.proc.poll() is None:
+            if os.path.getsize(self.path) > 0:
+                break
+            time.sleep(0.02)
+        self.skip = sum(1 for _ in open(self.path))
 
     def stop(self):
         if self.proc is None:
@@ -88,11 +97,14 @@ class Clocks:
             self.proc.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.proc.kill()
-        rows = []
-        for line in open(self.path):
+        rows, before = [], []
+        for k, line in enumerate(open(self.path)):
             parts = [p.strip() for p in line.split(",")]
             if len(parts) >= 9:
-                rows.append(parts)
+                (rows if k >= getattr(self, "skip", 0) else before).append(parts)
+        in_region = len(rows)
+        if not rows:    # a region shorter than one sampling interval
+            rows = before[-1:]
         os.unlink(self.path)
         if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
@@ -103,7 +115,7 @@ class Clocks:
                           if r[5 + i].lower().startswith("active")})
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
-                "samples": len(rows)}
+                "samples": len(rows), "samples_in_timed_region": in_region}
 
 
 def reduce_over_ranks(ms, count, device="cpu"):

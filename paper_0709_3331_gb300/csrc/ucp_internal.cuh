@@ -118,6 +118,10 @@ void launch_mac_prepare(Tree t, const Cube* cube, double theta, int want_f32, cu
 void launch_walk_fp64(const WalkArgs& a, int nsm, cudaStream_t s);
 void launch_walk_fp32c(const WalkArgs& a, int nsm, cudaStream_t s, int shape);
 int walk_shape_count();
+// Reorders a chunk list longest-first by the cost (20 per pair + 64 per multipole)
+// its targets had in the walk just finished; cost and tmp hold nchunks entries.
+void launch_chunk_order(int4* chunks, int nchunks, const int* targets, const int* cnt_p2p,
+                        const int* cnt_m2p, float* cost, int4* tmp, cudaStream_t s);
 
 // ---- adjoint (ucp_adjoint.cu) ----
 void launch_walk_adjoint(const WalkArgs& a, const double* lam, double* mu, double* adj, int nn_cap,

@@ -72,6 +72,8 @@ struct ucp_ctx {
     unsigned char* cloud = nullptr;    // cloud of each slot (batches only)
     int4* chunks_all = nullptr;        // walk chunks over all particles
     int4* chunks_e = nullptr;          // walk chunks over the compacted electrons
+    float* chunk_cost = nullptr;       // per chunk, for the longest-first order
+    int4* chunk_tmp = nullptr;
     int n_chunks_all = 0, n_chunks_e = 0, n_chunks_all_cap = 0;
     int sorted_buf = 0;                // key[] / val[] buffer of the last sort
     std::vector<double> cloud_energy;  // per-cloud {KE_i, KE_e, PE, px, py, pz} of the last energy
@@ -251,6 +253,9 @@ int force(ucp_ctx* c, double theta, double eps, int electrons_only, bool want_ph
         if (f32) launch_walk_fp32c(a, c->nsm, c->s, c->walk_shape);
         else launch_walk_fp64(a, c->nsm, c->s);
         prof_end(c);
+        // the next walk over the same targets takes its chunks longest-first
+        launch_chunk_order(electrons_only ? c->chunks_e : c->chunks_all, a.nchunks, a.targets,
+                           c->cnt_p2p, c->cnt_m2p, c->chunk_cost, c->chunk_tmp, c->s);
         c->walk_targets += a.ntargets;
         c->walk_launches += 1;
     }
@@ -495,7 +500,9 @@ int ucp_create_batch(ucp_ctx** out, const ucp_params* p, int32_t n_clouds, const
         for (int i = 0; i < n_clouds; ++i) nch += (sizes[i] + 31) / 32;
         c->n_chunks_all_cap = (int)nch;
         if ((rc = dalloc(c, &c->chunks_all, (size_t)nch)) ||
-            (rc = dalloc(c, &c->chunks_e, (size_t)nch)))
+            (rc = dalloc(c, &c->chunks_e, (size_t)nch)) ||
+            (rc = dalloc(c, &c->chunk_cost, (size_t)nch)) ||
+            (rc = dalloc(c, &c->chunk_tmp, (size_t)nch)))
             return bail(rc);
     }
     if ((rc = dalloc(c, &c->qsp, 2)) || (rc = dalloc(c, &c->msp, 2))) return bail(rc);
