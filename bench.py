@@ -354,6 +354,7 @@ def run_gpu(args):
                                                          "every timed step",
                    "walk_shape": {"index": shape, "threads": WALK_SHAPE_TABLE[shape][0],
                                   "blocks_per_sm": WALK_SHAPE_TABLE[shape][1],
+                                  "staged_leaf_sources": bool(WALK_SHAPE_TABLE[shape][2]),
                                   "autotune_ms_per_walk": shape_ms}},
         "particle_steps_per_s": pst,
         "p2p_pairs_per_s": float(st[0]) * ws / (ms_all / 1e3),

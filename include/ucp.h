@@ -158,11 +158,12 @@ int ucp_set_graphs(ucp_ctx* ctx, int enable);
 int ucp_autotune(ucp_ctx* ctx, double theta, double eps, int* best_shape, float* best_ms);
 
 /* Number of FP32C walk launch shapes, and a call that sets one directly
- * (0 = the default of 128 threads x 7 blocks per SM; UCP_EINVAL outside
+ * (0 = the default of 128 threads x 7 blocks per SM, leaf sources read
+ * through L1; UCP_EINVAL outside
  * [0, UCP_WALK_SHAPES)).  The trial walks of ucp_autotune overwrite the forces and
  * interaction counts read by ucp_get_counts, and the next ucp_step recomputes its
  * first forces. */
-#define UCP_WALK_SHAPES 6
+#define UCP_WALK_SHAPES 10
 int ucp_set_walk_shape(ucp_ctx* ctx, int shape);
 
 /* Sec. 5 observables of the current state: out = {KE_ion, KE_electron, PE,

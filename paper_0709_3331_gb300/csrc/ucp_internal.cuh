@@ -112,6 +112,7 @@ struct WalkArgs {
     double* ax; double* ay; double* az; double* phi;  // key order; phi may be NULL
     int* cnt_p2p; int* cnt_m2p;                        // key order
     int* work;              // dynamic work counter (zeroed before launch)
+    int* err;               // raised by a bounded wait that gave up
     unsigned long long* stats; // {p2p, m2p}
 };
 void launch_mac_prepare(Tree t, const Cube* cube, double theta, int want_f32, cudaStream_t s);

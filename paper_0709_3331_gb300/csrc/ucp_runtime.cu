@@ -245,6 +245,7 @@ int force(ucp_ctx* c, double theta, double eps, int electrons_only, bool want_ph
     a.cnt_p2p = c->cnt_p2p;
     a.cnt_m2p = c->cnt_m2p;
     a.work = c->work;
+    a.err = c->sort.err;
     a.stats = c->stats;
     cudaMemsetAsync(c->cnt_p2p, 0, sizeof(int) * (size_t)c->n, c->s);
     cudaMemsetAsync(c->cnt_m2p, 0, sizeof(int) * (size_t)c->n, c->s);
@@ -302,7 +303,7 @@ int device_error(ucp_ctx* c)
     int e = 0;
     if (cudaMemcpy(&e, c->sort.err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
         return fail(c, UCP_ECUDA, "reading the device error flag failed");
-    if (e) return fail(c, UCP_ETIMEOUT, "a device-side wait of the key sort gave up");
+    if (e) return fail(c, UCP_ETIMEOUT, "a bounded device-side wait gave up");
     return UCP_OK;
 }
 
@@ -977,6 +978,7 @@ int ucp_grad_ke_electrons(ucp_ctx* c, double dt_e, int kk, int64_t n_steps, doub
             a.kelbg = 0;
             a.lambda = 1.0;
             a.work = c->work;
+            a.err = c->sort.err;
             launch_walk_adjoint(a, lsorted, mu, adj, c->t.cap, c->nsm, c->s);
             launch_scatter_add3(mu, c->id[k], c->n, lx, c->s);
             if (g > 0) launch_axpy3(lv, lx, dt_e, c->n, c->s);  // drift g

@@ -22,7 +22,6 @@ namespace ucp {
 namespace {
 
 constexpr int kWalkThreads = 128;
-constexpr int kWalkWarps = kWalkThreads / 32;
 constexpr int kList = 64;      // opened leaves buffered per warp
 constexpr int kM2PBatch = 32;  // visits whose multipoles are summed in FP32 before a
                                // compensated add (a power of two)
@@ -48,6 +47,44 @@ __device__ __forceinline__ void two_sum_acc(float& s, float& c, float v)
     c += (s - ap) + (v - bp);
     s = t;
 }
+
+// ---- bulk copies (TMA) of a leaf's sources into shared memory, completion
+// tracked by an mbarrier (one arrival carrying the byte count)
+__device__ __forceinline__ unsigned int smem_addr(const void* p)
+{
+    return (unsigned int)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(unsigned long long* bar)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_init_fence()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+// generic-proxy reads of a buffer are ordered before the next bulk copy into it
+__device__ __forceinline__ void async_proxy_fence()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned int bytes,
+                                          unsigned long long* bar)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+                 ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_test(unsigned long long* bar, unsigned int parity)
+{
+    unsigned int ok;
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                 " selp.u32 %0, 1, 0, p;\n}"
+                 : "=r"(ok) : "r"(smem_addr(bar)), "r"(parity) : "memory");
+    return ok != 0;
+}
+constexpr int kStagePairs = 16;          // sources staged per leaf: up to 32 (16 pairs)
+constexpr int kStageSpin = 1 << 20;      // polls of a copy's barrier before giving up
 
 // ------------------------------------------------------------------ FP64
 // Expansion of a box at R = x_t - c, r2 = R.R + eps^2, g = r2^-1/2, u = g^2:
@@ -265,14 +302,29 @@ __device__ __forceinline__ void kelbg_pg(float u, float& p, float& g)
     }
 }
 
-// kThreads threads per block, register budget for kBlocks resident blocks per SM
-template <bool kKelbg, int kThreads, int kBlocks>
+// kThreads threads per block, register budget for kBlocks resident blocks per SM.
+// kStage: a leaf's sources (up to 32) are brought into shared memory by a bulk
+// copy issued one list entry ahead (double buffer per warp) instead of being read
+// through L1 by every lane; the arithmetic and its order are the same.
+template <bool kKelbg, int kThreads, int kBlocks, bool kStage>
 __global__ void __launch_bounds__(kThreads, kBlocks)
 k_walk_fp32c(WalkArgs a)
 {
     __shared__ WarpList L[kThreads / 32];
+    __shared__ __align__(16) float4 stage[kStage ? kThreads / 32 : 1][2][2 * kStagePairs];
+    __shared__ __align__(8) unsigned long long stage_bar[kStage ? kThreads / 32 : 1][2];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     WarpList& lst = L[w];
+    unsigned int stage_phase = 0;  // parity to wait for, per buffer (bits 0, 1)
+    bool stage_ok = kStage;        // cleared for good if a copy is not seen to complete
+    if (kStage) {
+        if (lane == 0) {
+            mbar_init(&stage_bar[w][0]);
+            mbar_init(&stage_bar[w][1]);
+            mbar_init_fence();
+        }
+        __syncwarp();
+    }
     const double q0 = a.qsp[0], q1 = a.qsp[1];
     const float4* __restrict__ F = a.t.f32;
     const float4* __restrict__ S = a.src32;
@@ -314,7 +366,95 @@ k_walk_fp32c(WalkArgs a)
             bx = by = bz = bp = 0.f;
         };
 
+        // one list entry's pair sum from sources at P0 (paired float4, P0[0] = the
+        // pair that holds source jb)
+        auto leaf_pairs = [&](int nd, const float4* __restrict__ P0) {
+            const float4* r = F + (size_t)nd * kF32;
+            float4 A = r[0], B = r[1], C = r[2];
+            float rx = (xh + A.x) + (xl + B.x);
+            float ry = (yh + A.y) + (yl + B.y);
+            float rz = (zh + A.z) + (zl + B.z);
+            int jb = __ldg(&a.t.info[nd].x), je = __float_as_int(C.y);
+            const float2 rx2 = make_float2(rx, rx), ry2 = make_float2(ry, ry),
+                         rz2 = make_float2(rz, rz), e2 = make_float2(eps2, eps2);
+            float2 px = make_float2(0.f, 0.f), py = px, pz = px, pp = px;
+#pragma unroll 2
+            for (int j = jb & ~1; j < je; j += 2) {
+                const float4 P = P0[j - (jb & ~1)], Q = P0[j - (jb & ~1) + 1];
+                float2 dx = __fadd2_rn(rx2, make_float2(P.x, P.y));
+                float2 dy = __fadd2_rn(ry2, make_float2(P.z, P.w));
+                float2 dz = __fadd2_rn(rz2, make_float2(Q.x, Q.y));
+                float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __ffma2_rn(dz, dz, e2)));
+                const bool ok0 = j >= jb && j != t;
+                const bool ok1 = j + 1 < je && j + 1 != t;
+                float2 ri = make_float2(ok0 ? rsqrtf(r2.x) : 0.f, ok1 ? rsqrtf(r2.y) : 0.f);
+                float2 qi = __fmul2_rn(make_float2(Q.z, Q.w), ri);
+                float2 qr3 = __fmul2_rn(__fmul2_rn(qi, ri), ri);
+                px = __ffma2_rn(qr3, dx, px);
+                py = __ffma2_rn(qr3, dy, py);
+                pz = __ffma2_rn(qr3, dz, pz);
+                pp = __fadd2_rn(pp, qi);
+            }
+            np += (je - jb) - ((t >= jb && t < je) ? 1 : 0);
+            two_sum_acc(sx, cx, px.x + px.y);
+            two_sum_acc(sy, cy, py.x + py.y);
+            two_sum_acc(sz, cz, pz.x + pz.y);
+            two_sum_acc(sp, cp, pp.x + pp.y);
+        };
+
+        // Staged form: entry e's sources go to buffer e & 1 while entry e - 1 is
+        // summed; entries with more than 32 sources read them from global memory.
+        auto stage_entry = [&](int e) -> bool {
+            const int nd = lst.leaf[e];
+            const int jb = __ldg(&a.t.info[nd].x);
+            const int je = __float_as_int(__ldg(&F[(size_t)nd * kF32 + 2]).y);
+            const int pb = jb >> 1, pe = (je + 1) >> 1;
+            if (!stage_ok || pe - pb > kStagePairs) return false;
+            if (lane == 0) {
+                async_proxy_fence();
+                bulk_load(&stage[w][e & 1][0], S + 2 * (size_t)pb,
+                          (unsigned int)(pe - pb) * 32u, &stage_bar[w][e & 1]);
+            }
+            return true;
+        };
+        auto flush_staged = [&]() {
+            __syncwarp();
+            bool st_cur = npl > 0 ? stage_entry(0) : false;
+            for (int e = 0; e < npl; ++e) {
+                bool st_next = e + 1 < npl ? stage_entry(e + 1) : false;
+                const int nd = lst.leaf[e];
+                const float4* P0;
+                if (st_cur) {
+                    const int b = e & 1;
+                    bool done = false;
+                    for (int it = 0; it < kStageSpin && !done; ++it)
+                        done = mbar_test(&stage_bar[w][b], (stage_phase >> b) & 1u);
+                    stage_phase ^= 1u << b;
+                    P0 = &stage[w][b][0];
+                    if (!done) {
+                        // raise the flag, stop staging in this warp and read this
+                        // entry from global memory
+                        if (lane == 0) atomicExch(a.err, 1);
+                        stage_ok = false;
+                        st_next = false;
+                        P0 = S + ((size_t)__ldg(&a.t.info[nd].x) & ~(size_t)1);
+                    }
+                } else {
+                    P0 = S + ((size_t)__ldg(&a.t.info[nd].x) & ~(size_t)1);
+                }
+                if ((lst.mask[e] >> lane) & 1u) leaf_pairs(nd, P0);
+                __syncwarp();
+                st_cur = st_next;
+            }
+            npl = 0;
+            __syncwarp();
+        };
+
         auto flush = [&]() {
+            if (kStage && !kKelbg) {
+                flush_staged();
+                return;
+            }
             __syncwarp();
             for (int e = 0; e < npl; ++e) {
                 int nd = lst.leaf[e];
@@ -563,22 +703,25 @@ void launch_walk_fp64(const WalkArgs& a, int nsm, cudaStream_t s)
 }
 
 // Launch shapes of the FP32C walk that the autotuner chooses from: threads per
-// block and resident blocks per SM, which also sets the register budget (28
-// warps per SM at 72 registers, 32 at 64).  The persistent grid takes 32-target
+// block, resident blocks per SM, which also sets the register budget (28 warps
+// per SM at 72 registers, 32 at 64), and whether leaf sources are staged in
+// shared memory by bulk copies.  The persistent grid takes 32-target
 // chunks from a counter, so the shape changes the schedule, never a result.
-static const int kShapes[][2] = {{128, 7}, {896, 1}, {128, 8}, {1024, 1}, {256, 4}, {512, 2}};
+static const int kShapes[][3] = {{128, 7, 0}, {896, 1, 0}, {128, 8, 0}, {1024, 1, 0},
+                                 {256, 4, 0}, {512, 2, 0}, {128, 7, 1}, {896, 1, 1},
+                                 {128, 8, 1}, {256, 4, 1}};
 int walk_shape_count() { return (int)(sizeof(kShapes) / sizeof(kShapes[0])); }
 
-template <bool kKelbg>
+template <bool kKelbg, bool kStage>
 static void walk_fp32c_shape(const WalkArgs& a, int th, int per_sm, int b, cudaStream_t s)
 {
-    if (th == 32) k_walk_fp32c<kKelbg, 32, 24><<<b, 32, 0, s>>>(a);
-    else if (th == 896) k_walk_fp32c<kKelbg, 896, 1><<<b, 896, 0, s>>>(a);
-    else if (th == 1024) k_walk_fp32c<kKelbg, 1024, 1><<<b, 1024, 0, s>>>(a);
-    else if (th == 256) k_walk_fp32c<kKelbg, 256, 4><<<b, 256, 0, s>>>(a);
-    else if (th == 512) k_walk_fp32c<kKelbg, 512, 2><<<b, 512, 0, s>>>(a);
-    else if (per_sm >= 8) k_walk_fp32c<kKelbg, 128, 8><<<b, 128, 0, s>>>(a);
-    else k_walk_fp32c<kKelbg, 128, 7><<<b, 128, 0, s>>>(a);
+    if (th == 32) k_walk_fp32c<kKelbg, 32, 24, false><<<b, 32, 0, s>>>(a);
+    else if (th == 896) k_walk_fp32c<kKelbg, 896, 1, kStage><<<b, 896, 0, s>>>(a);
+    else if (th == 1024) k_walk_fp32c<kKelbg, 1024, 1, false><<<b, 1024, 0, s>>>(a);
+    else if (th == 256) k_walk_fp32c<kKelbg, 256, 4, kStage><<<b, 256, 0, s>>>(a);
+    else if (th == 512) k_walk_fp32c<kKelbg, 512, 2, false><<<b, 512, 0, s>>>(a);
+    else if (per_sm >= 8) k_walk_fp32c<kKelbg, 128, 8, kStage><<<b, 128, 0, s>>>(a);
+    else k_walk_fp32c<kKelbg, 128, 7, kStage><<<b, 128, 0, s>>>(a);
 }
 
 void launch_walk_fp32c(const WalkArgs& a, int nsm, cudaStream_t s, int shape)
@@ -588,9 +731,12 @@ void launch_walk_fp32c(const WalkArgs& a, int nsm, cudaStream_t s, int shape)
     if (shape < 0 || shape >= walk_shape_count()) shape = 0;
     int th = kShapes[shape][0], b;
     const int per_sm = kShapes[shape][1];
+    // the Kelbg pair law reads its sources directly
+    const bool stage = kShapes[shape][2] != 0 && !a.kelbg;
     walk_grid(a.nchunks, nsm, &th, per_sm, &b);
-    if (a.kelbg) walk_fp32c_shape<true>(a, th, per_sm, b, s);
-    else walk_fp32c_shape<false>(a, th, per_sm, b, s);
+    if (a.kelbg) walk_fp32c_shape<true, false>(a, th, per_sm, b, s);
+    else if (stage) walk_fp32c_shape<false, true>(a, th, per_sm, b, s);
+    else walk_fp32c_shape<false, false>(a, th, per_sm, b, s);
 }
 
 }  // namespace ucp

@@ -20,9 +20,11 @@ UCP_OK, UCP_EINVAL, UCP_ENOMEM, UCP_ECUDA, UCP_ENONFINITE, UCP_ETIMEOUT, UCP_EST
 UCP_FP64, UCP_FP32C = 0, 1
 UCP_ION, UCP_ELECTRON = 0, 1
 UCP_POT_PLUMMER, UCP_POT_KELBG = 0, 1
-UCP_WALK_SHAPES = 6
-# (threads per block, blocks per SM) of each FP32C walk launch shape
-WALK_SHAPE_TABLE = ((128, 7), (896, 1), (128, 8), (1024, 1), (256, 4), (512, 2))
+UCP_WALK_SHAPES = 10
+# (threads per block, blocks per SM, leaf sources staged by bulk copies) of each
+# FP32C walk launch shape
+WALK_SHAPE_TABLE = ((128, 7, 0), (896, 1, 0), (128, 8, 0), (1024, 1, 0), (256, 4, 0), (512, 2, 0),
+                    (128, 7, 1), (896, 1, 1), (128, 8, 1), (256, 4, 1))
 
 EXPORTS = ("ucp_create", "ucp_destroy", "ucp_set_state", "ucp_get_state", "ucp_tree_build",
            "ucp_tree_force", "ucp_step", "ucp_energy", "ucp_stats", "ucp_get_cube",

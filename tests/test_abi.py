@@ -85,9 +85,10 @@ def test_walk_shape_count_matches_header():
     m = re.search(r"#define UCP_WALK_SHAPES (\d+)", src)
     assert m and int(m.group(1)) == ucp.UCP_WALK_SHAPES
     cu = open(os.path.join(ROOT, "paper_0709_3331_gb300", "csrc", "ucp_walk.cu")).read()
-    tab = re.search(r"kShapes\[\]\[2\] = \{(.*?)\};", cu).group(1)
-    pairs = tuple((int(a), int(b)) for a, b in re.findall(r"\{(\d+), (\d+)\}", tab))
-    assert pairs == ucp.WALK_SHAPE_TABLE and len(pairs) == ucp.UCP_WALK_SHAPES
+    tab = re.search(r"kShapes\[\]\[3\] = \{(.*?)\};", cu, flags=re.S).group(1)
+    rows = tuple((int(a), int(b), int(c)) for a, b, c in
+                 re.findall(r"\{(\d+), (\d+), (\d+)\}", tab))
+    assert rows == ucp.WALK_SHAPE_TABLE and len(rows) == ucp.UCP_WALK_SHAPES
 
 
 def test_walk_shape_rejects_null_context(L):
