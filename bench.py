@@ -491,9 +491,32 @@ def run_extras(c, W, ws, pos_d, vel_d, sp_d, Context, UCP_FP32C, UCP_FP64, timed
         / (wmb / 1e3) / 1e12 / peak,
         "walk_shape": WALK_SHAPE_TABLE[bshape],
         "step": "one block of 10 electron substeps for all 64 clouds, theta 0.5, FP32C"}
+    # the same ensemble for 500 electron substeps, each block a captured CUDA graph
+    cb.set_graphs(True)
+    cb.set_state(bpos, bvel, bsp)
+    en0 = cb.energy_clouds(0.5, W["eps"])
+    cb.step(W["dt_e"], W["k"], W["k"], 0.5, W["eps"])       # captures the block graph
+    cb.stats(reset=True)
+    torch.cuda.synchronize()
+    g0 = torch.cuda.Event(enable_timing=True)
+    g1 = torch.cuda.Event(enable_timing=True)
+    g0.record(stream)
+    cb.step(W["dt_e"], W["k"], 490, 0.5, W["eps"])
+    g1.record(stream)
+    torch.cuda.synchronize()
+    msg = g0.elapsed_time(g1)
+    stg = cb.stats(reset=True)
+    en1 = cb.energy_clouds(0.5, W["eps"])
+    drift = np.abs(en1[:, 3] - en0[:, 3]) / (en0[:, 0] + en0[:, 1] + np.abs(en0[:, 2]))
+    extra["batched_64_clouds"]["graphs_500_substeps"] = {
+        "ms_per_block": msg / 49, "interactions_per_s": float(stg[0] + stg[1]) / (msg / 1e3),
+        "particle_steps_per_s": ntot * 490 / (msg / 1e3),
+        "energy_drift_max_over_clouds": float(drift.max()),
+        "energy_drift_median": float(np.median(drift)),
+        "note": "500 electron substeps: 1 block to capture the graph, 49 timed replays"}
     cb.close()
 
-    # plain method in FP64: N = 131072, sigma 4, 100 electron substeps (10 blocks)
+    # plain method in FP64: N = 131072, sigma 4, 1000 electron substeps (100 blocks)
     c1 = gaussian_cloud(131072, 4.0, 2)
     cp = Context(c1.n, c1.q, c1.m, leaf_cap=W["leaf_cap"], precision=UCP_FP64)
     cp.set_state(c1.pos, c1.vel, c1.species)
@@ -502,14 +525,14 @@ def run_extras(c, W, ws, pos_d, vel_d, sp_d, Context, UCP_FP32C, UCP_FP64, timed
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
     t0.record(stream)
-    cp.step(W["dt_e"], W["k"], 100, 0.5, W["eps"])
+    cp.step(W["dt_e"], W["k"], 1000, 0.5, W["eps"])
     t1.record(stream)
     torch.cuda.synchronize()
     mp = t0.elapsed_time(t1)
     e1 = cp.energy(0.5, W["eps"])
     # differentiation form: N = 262144 (sigma 6), FP32C forces with FP64 state,
     # gradient of the final electron kinetic energy w.r.t. the initial state
-    # (40 electron substeps, checkpoint every 20), against the forward alone
+    # (200 electron substeps, checkpoint every 20), against the forward alone
     c4 = gaussian_cloud(262144, 6.0, 5)
     ca = Context(c4.n, c4.q, c4.m, leaf_cap=W["leaf_cap"], precision=UCP_FP32C)
     p4 = torch.from_numpy(c4.pos).cuda()
@@ -520,20 +543,20 @@ def run_extras(c, W, ws, pos_d, vel_d, sp_d, Context, UCP_FP32C, UCP_FP64, timed
     ca.set_state(p4, v4, s4)
     torch.cuda.synchronize()
     w0 = time.perf_counter()
-    ca.step(W["dt_e"], W["k"], 40, 0.5, W["eps"])
+    ca.step(W["dt_e"], W["k"], 200, 0.5, W["eps"])
     torch.cuda.synchronize()
     t_fwd = time.perf_counter() - w0
     ca.set_state(p4, v4, s4)
     torch.cuda.synchronize()
     w0 = time.perf_counter()
-    L4, _, _ = ca.grad_ke_electrons(W["dt_e"], W["k"], 40, 0.5, W["eps"], 20, gx4, gv4)
+    L4, _, _ = ca.grad_ke_electrons(W["dt_e"], W["k"], 200, 0.5, W["eps"], 20, gx4, gv4)
     torch.cuda.synchronize()
     t_grad = time.perf_counter() - w0
     extra["adjoint_n262144"] = {
-        "electron_steps": 40, "checkpoint_every": 20, "forward_s": t_fwd, "gradient_s": t_grad,
+        "electron_steps": 200, "checkpoint_every": 20, "forward_s": t_fwd, "gradient_s": t_grad,
         "gradient_over_forward": t_grad / t_fwd, "loss": L4,
         "note": "gradient time includes the forward run, the checkpointed recomputation and "
-                "41 FP32 adjoint walks"}
+                "201 FP32 adjoint walks"}
     ca.close()
 
     # the small workload (N = 2048, sigma 1, FP64): launch-bound, so each block of
@@ -567,7 +590,7 @@ def run_extras(c, W, ws, pos_d, vel_d, sp_d, Context, UCP_FP32C, UCP_FP64, timed
     extra["plain_fp64_n2048"] = small
 
     extra["plain_fp64_n131072"] = {
-        "electron_steps": 100, "ms": mp, "particle_steps_per_s": c1.n * 100 / (mp / 1e3),
+        "electron_steps": 1000, "ms": mp, "particle_steps_per_s": c1.n * 1000 / (mp / 1e3),
         "energy_drift": abs(e1[3] - e0[3]) / (e0[0] + e0[1] + abs(e0[2]))}
     cp.close()
     return extra
