@@ -187,7 +187,9 @@ def run_reference(args):
     c = gaussian_cloud(WORKLOAD["n"], WORKLOAD["sigma"], WORKLOAD["seed"])
     cores = os.cpu_count() or 1
     nthreads = cores if O.has_openmp() else 1
-    nt = 4096
+    # a step: one tree build over every particle and a walk over an eighth of them
+    # (a substep builds once and walks the N/2 electrons)
+    nt = WORKLOAD["n"] // 8
     for _ in range(args.warmup):
         oracle_sample(c, 512, nthreads)
     tot_t, tot_i = 0.0, 0
