@@ -272,15 +272,35 @@ int force(ucp_ctx* c, double theta, double eps, int electrons_only, bool want_ph
 // Walk chunks: up to 32 consecutive targets of one cloud.  All-particle chunks
 // cover each cloud's segment; electron chunks cover each cloud's run in the
 // compacted electron list (electrons keep their cloud order under sorting).
+// Targets per walk chunk: 32 (one per lane).  An FP64 context too small to give
+// every SM two chunks takes narrower chunks (down to 8 targets), so more warps
+// share the latency-bound FP64 walk; its sums do not depend on which targets
+// share a warp, so the results are the same.  The FP32C walk's batched sums do
+// depend on the warp's company, so it keeps 32.
+static int chunk_width(ucp_ctx* c)
+{
+    if (c->precision != UCP_FP64) return 32;
+    int w = 32;
+    while (w > 8) {
+        int64_t nch = 0;
+        for (int cl = 0; cl < c->n_clouds; ++cl)
+            nch += (c->cloud_start_h[cl + 1] - c->cloud_start_h[cl] + w - 1) / w;
+        if (nch >= 2 * (int64_t)c->nsm) break;
+        w /= 2;
+    }
+    return w;
+}
+
 int build_chunks(ucp_ctx* c, const std::vector<int>& ne_per_cloud)
 {
     std::vector<int4> all, el;
     int e0 = 0;
+    const int W = chunk_width(c);
     for (int cl = 0; cl < c->n_clouds; ++cl) {
         int b = c->cloud_start_h[cl], e = c->cloud_start_h[cl + 1];
-        for (int t = b; t < e; t += 32) all.push_back(make_int4(t, std::min(32, e - t), cl, 0));
+        for (int t = b; t < e; t += W) all.push_back(make_int4(t, std::min(W, e - t), cl, 0));
         int ne = ne_per_cloud[cl];
-        for (int t = 0; t < ne; t += 32) el.push_back(make_int4(e0 + t, std::min(32, ne - t), cl, 0));
+        for (int t = 0; t < ne; t += W) el.push_back(make_int4(e0 + t, std::min(W, ne - t), cl, 0));
         e0 += ne;
     }
     if ((int)all.size() > c->n_chunks_all_cap || (int)el.size() > c->n_chunks_all_cap)
@@ -498,7 +518,7 @@ int ucp_create_batch(ucp_ctx** out, const ucp_params* p, int32_t n_clouds, const
             c->t.cloud = c->cloud;
         }
         int64_t nch = 0;
-        for (int i = 0; i < n_clouds; ++i) nch += (sizes[i] + 31) / 32;
+        for (int i = 0; i < n_clouds; ++i) nch += (sizes[i] + 7) / 8;  // chunks of >= 8
         c->n_chunks_all_cap = (int)nch;
         if ((rc = dalloc(c, &c->chunks_all, (size_t)nch)) ||
             (rc = dalloc(c, &c->chunks_e, (size_t)nch)) ||

@@ -171,7 +171,10 @@ k_walk_fp64(WalkArgs a)
         const int end = info[root].z;
         const double xt = valid ? X[t] : 0.0, yt = valid ? Y[t] : 0.0, zt = valid ? Z[t] : 0.0;
         const int8_t st = valid ? SP[t] : 0;
+        // multipole and direct-pair sums kept apart: each is then a sum over this
+        // target's own boxes in pre-order, whichever targets share the warp
         double ex = 0.0, ey = 0.0, ez = 0.0, ph = 0.0;
+        double pex = 0.0, pey = 0.0, pez = 0.0, pph = 0.0;
         int np = 0, nm = 0;
         int skip = valid ? 0 : 0x7fffffff;
         int npl = 0;
@@ -192,25 +195,25 @@ k_walk_fp64(WalkArgs a)
                             double r = sqrt(dx * dx + dy * dy + dz * dz);
                             ++np;
                             if (r == 0.0) {
-                                ph += qj / a.lambda;
+                                pph += qj / a.lambda;
                                 continue;
                             }
                             double u = r / a.lambda;
                             double e = exp(-u), ome = -expm1(-u);
                             double f = ome / (r * r * r) - e / (a.lambda * r * r);
-                            ex += qj * dx * f;
-                            ey += qj * dy * f;
-                            ez += qj * dz * f;
-                            ph += qj * ome / r;
+                            pex += qj * dx * f;
+                            pey += qj * dy * f;
+                            pez += qj * dz * f;
+                            pph += qj * ome / r;
                             continue;
                         }
                         double r2 = dx * dx + dy * dy + dz * dz + a.eps2;
                         double ri = rsqrt(r2);
                         double qr3 = qj * ri * ri * ri;
-                        ex += qr3 * dx;
-                        ey += qr3 * dy;
-                        ez += qr3 * dz;
-                        ph += qj * ri;
+                        pex += qr3 * dx;
+                        pey += qr3 * dy;
+                        pez += qr3 * dz;
+                        pph += qj * ri;
                         ++np;
                     }
                 }
@@ -260,10 +263,10 @@ k_walk_fp64(WalkArgs a)
         if (valid) {
             const int s = SP[t];
             const double qm = (s ? q1 : q0) / a.msp[s];
-            a.ax[t] = qm * ex;
-            a.ay[t] = qm * ey;
-            a.az[t] = qm * ez;
-            if (a.phi) a.phi[t] = ph;
+            a.ax[t] = qm * (ex + pex);
+            a.ay[t] = qm * (ey + pey);
+            a.az[t] = qm * (ez + pez);
+            if (a.phi) a.phi[t] = ph + pph;
             a.cnt_p2p[t] = np;
             a.cnt_m2p[t] = nm;
         }
