@@ -61,3 +61,31 @@ def test_autotune_keeps_trajectory(U):
             ctx.step(1e-3, 5, 10, 0.5, 0.01)
             out.append(ctx.get_state())
     assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+
+
+@pytest.mark.parametrize("case", ["leaf_cap_32", "fat_leaf"])
+def test_staged_sources_edge_sizes(U, orc, case):
+    """Leaves at the staging buffer's size (32 sources, with odd first index: 17
+    pairs, read from global memory) and a depth-21 box of 100 coincident particles
+    give the same bits in every shape, and match the oracle."""
+    from paper_0709_3331_gb300.ucp import UCP_WALK_SHAPES
+    c = gaussian_cloud(6000, 2.0, 17)
+    pos = c.pos.copy()
+    leaf_cap = 32
+    if case == "fat_leaf":
+        pos[:100] = pos[0]
+        leaf_cap = 16
+    with U.Context(c.n, c.q, c.m, leaf_cap=leaf_cap, precision=1) as ctx:
+        ctx.set_state(pos, c.vel, c.species)
+        ref = _walk(ctx, 0.5, 0.05)
+        for sh in range(1, UCP_WALK_SHAPES):
+            ctx.set_walk_shape(sh)
+            got = _walk(ctx, 0.5, 0.05)
+            for x, y in zip(got, ref):
+                assert np.array_equal(x, y), sh
+        if case == "fat_leaf":
+            assert ctx.get_tree()["depth"].max() == 21
+    E, _ = orc.Tree(pos, c.species, c.q, leaf_cap=leaf_cap).force(0.5, 0.05, nthreads=4)
+    a_ref = E * (c.q[c.species] / c.m[c.species])[:, None]
+    err = np.sqrt(((ref[0] - a_ref) ** 2).sum() / (a_ref ** 2).sum())
+    assert err <= 1e-4
