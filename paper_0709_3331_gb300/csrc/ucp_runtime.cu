@@ -86,6 +86,7 @@ struct ucp_ctx {
     // captured blocks of the split-step push (ucp_set_graphs)
     struct GraphEntry {
         int kk, cur_in, cur_out;
+        int n_e, n_chunks_all, n_chunks_e;  // launch parameters a new state can change
         double dt_e, theta, eps;
         cudaGraphExec_t exec;
         unsigned long long launches;
@@ -737,7 +738,9 @@ static int run_block_graph(ucp_ctx* c, double dt_e, int kk, double theta, double
 {
     ucp_ctx::GraphEntry* hit = nullptr;
     for (auto& g : c->graphs)
-        if (g.kk == kk && g.cur_in == c->cur && g.dt_e == dt_e && g.theta == theta && g.eps == eps)
+        if (g.kk == kk && g.cur_in == c->cur && g.n_e == c->n_e &&
+            g.n_chunks_all == c->n_chunks_all && g.n_chunks_e == c->n_chunks_e &&
+            g.dt_e == dt_e && g.theta == theta && g.eps == eps)
             hit = &g;
     if (!hit) {
         if (!c->cap_stream && cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking))
@@ -772,7 +775,8 @@ static int run_block_graph(ucp_ctx* c, double dt_e, int kk, double theta, double
         ec = cudaGraphInstantiate(&exec, graph, 0);
         cudaGraphDestroy(graph);
         if (ec != cudaSuccess) return fail(c, UCP_ECUDA, "graph instantiation failed");
-        c->graphs.push_back({kk, cur0, cur1, dt_e, theta, eps, exec, nl});
+        c->graphs.push_back({kk, cur0, cur1, c->n_e, c->n_chunks_all, c->n_chunks_e, dt_e, theta,
+                             eps, exec, nl});
         hit = &c->graphs.back();
     }
     CK(cudaGraphLaunch(hit->exec, c->s));

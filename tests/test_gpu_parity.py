@@ -1,7 +1,7 @@
 """GPU path vs the FP64 CPU oracle on the same seeded inputs, through the C ABI.
 
 Bars: integer work (cube, keys, sort order, box table) bit-exact; FP64 force
-relative RMS <= 1e-5 and FP32C <= 1e-4 against the oracle tree (north-star
+relative RMS <= 1e-5 and FP32C <= 1e-4 against the oracle tree (the stated
 tolerances), per-target interaction counts identical up to opening decisions
 that sit within rounding of the criterion; short trajectories pointwise.
 """
@@ -441,6 +441,24 @@ def test_graph_blocks_identical(U, prec, k):
     assert np.array_equal(res[0][0], res[1][0]) and np.array_equal(res[0][1], res[1][1])
     assert np.array_equal(res[0][2], res[1][2])
     assert np.array_equal(res[0][3][:4], res[1][3][:4])
+
+
+def test_graph_blocks_after_new_state(U):
+    """A captured block is replayed only for launches it fits: a new state with a
+    different electron count takes a new capture and matches a run without
+    graphs."""
+    c = gaussian_cloud(3000, 1.5, 62)
+    sp2 = c.species.copy()
+    sp2[:200] = 1          # 200 ions become electrons: other electron chunk count
+    res = []
+    for graphs in (False, True):
+        with _ctx(U, c, 16, 1) as ctx:
+            ctx.set_graphs(graphs)
+            ctx.step(1e-3, 5, 10, 0.5, 0.01)
+            ctx.set_state(c.pos, c.vel, sp2)
+            ctx.step(1e-3, 5, 10, 0.5, 0.01)
+            res.append(ctx.get_state())
+    assert np.array_equal(res[0][0], res[1][0]) and np.array_equal(res[0][1], res[1][1])
 
 
 def test_graph_blocks_batch(U):
