@@ -23,9 +23,9 @@ constexpr int kMom = 16;
 enum MomIdx { MC = 0, MR2 = 3, MM = 4, MD = 5, MQ = 8, MS0 = 14, MDELTA = 15 };
 
 // One FP32C box record, 5 float4 (80 B):
-//   A = {ch.x, ch.y, ch.z, rcrit2}   ch = fp32(c), cl = fp32(c - ch)
-//   B = {cl.x, cl.y, cl.z, bits(next)}
-//   C = {bits(begin), bits(end or -1 for a twig), M, D.x}
+//   A = {-ch.x, -ch.y, -ch.z, rcrit2}   ch = fp32(c), cl = fp32(c - ch)
+//   B = {-cl.x, -cl.y, -cl.z, bits(next)}
+//   C = {-tr(Q)/2, bits(end or -1 for a twig), M, D.x}
 //   D = {D.y, D.z, Qxx, Qxy}
 //   E = {Qxz, Qyy, Qyz, Qzz}
 constexpr int kF32 = 5;
