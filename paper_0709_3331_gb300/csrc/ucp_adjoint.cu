@@ -228,11 +228,58 @@ k_walk_adjoint(WalkArgs a, const double* __restrict__ lam, double* __restrict__ 
 // ---- FP32 form (FP32C contexts): the node-relative coordinates, records and
 // borderline FP64 decisions of the FP32C walk; per-lane sums in FP32, the
 // scatter into mu in FP64, the box accumulators in FP32.
-__device__ __forceinline__ float wsumf(float v)
+
+// Warp sums of several values at once by halving exchanges: at each xor step a
+// lane keeps half of its values and adds the partner's copy of that half, so 16
+// values take 16 exchanges instead of 80 (4 values: 6 instead of 20), and the
+// sums end up spread over the lanes.
+// 16 values: lane L ends with value 8 b4 + 4 b3 + 2 b2 + b1 (b_k = bit k of L)
+__device__ __forceinline__ float warp_sum16(float (&v)[16], int lane)
 {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
+    for (int i = 0; i < 8; ++i) {
+        const bool hi = (lane & 16) != 0;
+        const float keep = hi ? v[i + 8] : v[i], send = hi ? v[i] : v[i + 8];
+        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const bool hi = (lane & 8) != 0;
+        const float keep = hi ? v[i + 4] : v[i], send = hi ? v[i] : v[i + 4];
+        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const bool hi = (lane & 4) != 0;
+        const float keep = hi ? v[i + 2] : v[i], send = hi ? v[i] : v[i + 2];
+        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+    }
+    {
+        const bool hi = (lane & 2) != 0;
+        const float keep = hi ? v[1] : v[0], send = hi ? v[0] : v[1];
+        v[0] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
+    }
+    return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
+}
+
+// 4 values: lane L ends with value 2 b4 + b3
+__device__ __forceinline__ float warp_sum4(float (&v)[4], int lane)
+{
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const bool hi = (lane & 16) != 0;
+        const float keep = hi ? v[i + 2] : v[i], send = hi ? v[i] : v[i + 2];
+        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+    }
+    {
+        const bool hi = (lane & 8) != 0;
+        const float keep = hi ? v[1] : v[0], send = hi ? v[0] : v[1];
+        v[0] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    }
+    float r = v[0];
+#pragma unroll
+    for (int o = 4; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+    return r;
 }
 
 __device__ __forceinline__ float dot3f(const float* a, const float* b)
@@ -329,14 +376,11 @@ k_walk_adjoint_f32(WalkArgs a, const double* __restrict__ lam, double* __restric
                         sy = -qj * (wv[1] * g3 - 3.f * r3[1] * rw * g5);
                         sz = -qj * (wv[2] * g3 - 3.f * r3[2] * rw * g5);
                     }
-                    sx = wsumf(sx);
-                    sy = wsumf(sy);
-                    sz = wsumf(sz);
-                    if (lane == 0) {
-                        atomicAdd(&mu[3 * (size_t)j], (double)sx);
-                        atomicAdd(&mu[3 * (size_t)j + 1], (double)sy);
-                        atomicAdd(&mu[3 * (size_t)j + 2], (double)sz);
-                    }
+                    float sv[4] = {sx, sy, sz, 0.f};
+                    const float tot = warp_sum4(sv, lane);
+                    const int comp = ((lane >> 4) & 1) * 2 + ((lane >> 3) & 1);
+                    if ((lane & 7) == 0 && comp < 3)
+                        atomicAdd(&mu[3 * (size_t)j + comp], (double)tot);
                 }
             }
             npl = 0;
@@ -414,10 +458,13 @@ k_walk_adjoint_f32(WalkArgs a, const double* __restrict__ lam, double* __restric
                                      3.f * (wv[e] * R[c] + wv[c] * R[e] + (e == c ? Rw : 0.f)) * g5;
                     }
                 }
+                float sv[16];
 #pragma unroll
-                for (int k = 0; k < 12; ++k) src[k] = wsumf(src[k]);
-                if (lane == 0)
-                    for (int k = 0; k < 12; ++k) atomicAdd(&adj[(size_t)node * 12 + k], src[k]);
+                for (int k = 0; k < 16; ++k) sv[k] = k < 12 ? src[k] : 0.f;
+                const float tot = warp_sum16(sv, lane);
+                const int term = ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 +
+                                 ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1);
+                if ((lane & 1) == 0 && term < 12) atomicAdd(&adj[(size_t)node * 12 + term], tot);
             }
             node = next;
             if (npl == kAdjList) flush();
