@@ -294,18 +294,31 @@ __device__ __forceinline__ void qmulf(const float* Q, const float* v, float* o)
     o[2] = fmaf(Q[2], v[0], fmaf(Q[4], v[1], Q[5] * v[2]));
 }
 
-__device__ __forceinline__ void t4f(const float* R, const float* v, const float* Q, float g, float* o)
+// The fourth-derivative term of the expansion contracted with two vectors v1, v2
+// (one tensor, shared parts formed once):
+//   o_a = 105 R_a (R.v)(R.Q.R) g^9 - 15 g^7 (v_a R.Q.R + 2 (R.v)(QR)_a + 2 R_a v.QR
+//         + R_a (R.v) tr Q) + 3 g^5 (v_a tr Q + 2 (Qv)_a),
+// collected as coefficients of R_a, (QR)_a, v_a and (Qv)_a.
+__device__ __forceinline__ void t4f2(const float* R, const float* v1, const float* v2,
+                                     const float* Q, float g5, float g7, float g9, float Rv1,
+                                     float Rv2, float* o1, float* o2)
 {
-    float g2 = g * g, g5 = g2 * g2 * g, g7 = g5 * g2, g9 = g7 * g2;
-    float QR[3], Qv[3];
+    float QR[3];
     qmulf(Q, R, QR);
-    qmulf(Q, v, Qv);
-    float RQR = dot3f(R, QR), Rv = dot3f(R, v), vQR = dot3f(v, QR), trQ = Q[0] + Q[3] + Q[5];
+    const float RQR = dot3f(R, QR), trQ = Q[0] + Q[3] + Q[5];
+    const float cv = 3.f * g5 * trQ - 15.f * g7 * RQR;
+    const float cqv = 6.f * g5;
+    auto one = [&](const float* v, float Rv, float* o) {
+        float Qv[3];
+        qmulf(Q, v, Qv);
+        const float vQR = dot3f(v, QR);
+        const float cr = 105.f * Rv * RQR * g9 - 15.f * g7 * (2.f * vQR + Rv * trQ);
+        const float cq = -30.f * g7 * Rv;
 #pragma unroll
-    for (int a = 0; a < 3; ++a)
-        o[a] = 105.f * R[a] * Rv * RQR * g9 -
-               15.f * g7 * (v[a] * RQR + 2.f * Rv * QR[a] + 2.f * R[a] * vQR + R[a] * Rv * trQ) +
-               3.f * g5 * (v[a] * trQ + 2.f * Qv[a]);
+        for (int a = 0; a < 3; ++a) o[a] = fmaf(cr, R[a], fmaf(cq, QR[a], fmaf(cv, v[a], cqv * Qv[a])));
+    };
+    one(v1, Rv1, o1);
+    one(v2, Rv2, o2);
 }
 
 __global__ void __launch_bounds__(kAdjThreads)
@@ -431,20 +444,20 @@ k_walk_adjoint_f32(WalkArgs a, const double* __restrict__ lam, double* __restric
                     const float D[3] = {C.w, D4.x, D4.y};
                     const float Q[6] = {D4.z, D4.w, E4.x, E4.y, E4.z, E4.w};
                     const float g = rsqrtf(d2 + eps2);
-                    const float g2 = g * g, g3 = g2 * g, g5 = g3 * g2, g7 = g5 * g2;
+                    const float g2 = g * g, g3 = g2 * g, g5 = g3 * g2, g7 = g5 * g2, g9 = g7 * g2;
                     const float Rl = dot3f(R, l), RD = dot3f(R, D), lD = dot3f(l, D);
-                    float T4l[3];
-                    t4f(R, l, Q, g, T4l);
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) {
-                        float hess = M * (3.f * R[c] * Rl * g5 - l[c] * g3);
-                        float dterm = -15.f * R[c] * Rl * RD * g7 +
-                                      3.f * (l[c] * RD + D[c] * Rl + R[c] * lD) * g5;
-                        mt[c] -= qm * (hess - dterm + 0.5f * T4l[c]);
-                    }
                     const float Rw = dot3f(R, wv);
-                    float T4w[3];
-                    t4f(R, wv, Q, g, T4w);
+                    float T4l[3], T4w[3];
+                    t4f2(R, l, wv, Q, g5, g7, g9, Rl, Rw, T4l, T4w);
+                    // monopole Hessian M (3 R (R.l) g^5 - l g^3) minus the dipole term
+                    // -15 R (R.l)(R.D) g^7 + 3 (l (R.D) + D (R.l) + R (l.D)) g^5,
+                    // collected as coefficients of R, l and D
+                    const float aR = 3.f * g5 * (M * Rl - lD) + 15.f * g7 * Rl * RD;
+                    const float al = -(M * g3 + 3.f * g5 * RD);
+                    const float aD = -3.f * g5 * Rl;
+#pragma unroll
+                    for (int c = 0; c < 3; ++c)
+                        mt[c] -= qm * fmaf(aR, R[c], fmaf(al, l[c], fmaf(aD, D[c], 0.5f * T4l[c])));
 #pragma unroll
                     for (int c = 0; c < 3; ++c) {
                         src[c] = 3.f * R[c] * Rw * g5 - wv[c] * g3;
