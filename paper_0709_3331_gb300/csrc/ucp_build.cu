@@ -509,6 +509,19 @@ __global__ void k_topo_count(const unsigned long long* __restrict__ K, int n, in
     cnt[i] = c;
 }
 
+// atomicAdd(ctr, 1) for every calling lane, one atomic per distinct counter in
+// the warp (the lanes that add to the same counter take consecutive slots)
+__device__ __forceinline__ int warp_inc(int* ctr)
+{
+    const unsigned int active = __activemask();
+    const unsigned int peers = __match_any_sync(active, (unsigned long long)ctr);
+    const int lane = threadIdx.x & 31, leader = __ffs(peers) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(ctr, __popc(peers));
+    base = __shfl_sync(peers, base, leader);
+    return base + __popc(peers & ((1u << lane) - 1u));
+}
+
 __global__ void k_topo_emit(const unsigned long long* __restrict__ K, int n, int leaf_cap,
                             const int* __restrict__ cnt, const int* __restrict__ off, Tree t)
 {
@@ -540,8 +553,10 @@ __global__ void k_topo_emit(const unsigned long long* __restrict__ K, int n, int
         t.depth_leaf[node] = d | (leaf ? 256 : 0);
         t.cell[node] = pre;
         if (parent >= 0) t.child8[(size_t)parent * 8 + (int)(pre & 7ull)] = node;
-        if (leaf) t.leaf_list[atomicAdd(&t.count[kMaxDepth + 1], 1)] = node;
-        else t.twig_list[t.twig_off[d] + atomicAdd(&t.count[d], 1)] = node;
+        int* ctr = &t.count[leaf ? kMaxDepth + 1 : d];
+        const int slot = warp_inc(ctr);
+        if (leaf) t.leaf_list[slot] = node;
+        else t.twig_list[t.twig_off[d] + slot] = node;
         parent = node;
         ++node;
         dmax = d;
