@@ -88,8 +88,11 @@ struct ucp_ctx {
         int kk, cur_in, cur_out;
         int n_e, n_chunks_all, n_chunks_e;  // launch parameters a new state can change
         double dt_e, theta, eps;
+        bool prof;                          // walks bracketed by event-record nodes
+        cudaGraph_t graph;                  // kept while exec lives (its nodes are re-pointed)
         cudaGraphExec_t exec;
         unsigned long long launches;
+        std::vector<cudaGraphNode_t> ev_nodes;  // {begin, end} per walk, in walk order
     };
     bool use_graphs = false;
     int walk_shape = 0;                // launch shape of the FP32C walk (ucp_autotune)
@@ -97,6 +100,10 @@ struct ucp_ctx {
     std::vector<GraphEntry> graphs;
 
     bool prof = false;
+    // while a profiled block is captured: placeholder events, recorded as graph nodes
+    bool cap_prof = false;
+    std::vector<cudaEvent_t> cap_ev;
+    size_t cap_ev_used = 0;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
     size_t ev_used = 0;
     double prof_ms = 0.0;
@@ -158,9 +165,24 @@ int64_t box_capacity(int64_t n, int leaf_cap)
     return total < 1 ? 1 : total;
 }
 
+// the next placeholder event of a capture (event-record node in the graph)
+static void cap_record(ucp_ctx* c)
+{
+    if (c->cap_ev_used == c->cap_ev.size()) {
+        cudaEvent_t e;
+        cudaEventCreate(&e);
+        c->cap_ev.push_back(e);
+    }
+    cudaEventRecordWithFlags(c->cap_ev[c->cap_ev_used++], c->s, cudaEventRecordExternal);
+}
+
 void prof_begin(ucp_ctx* c)
 {
     if (!c->prof) return;
+    if (c->cap_prof) {
+        cap_record(c);
+        return;
+    }
     if (c->ev_used == c->ev.size()) {
         cudaEvent_t a, b;
         cudaEventCreate(&a);
@@ -173,6 +195,10 @@ void prof_begin(ucp_ctx* c)
 void prof_end(ucp_ctx* c)
 {
     if (!c->prof) return;
+    if (c->cap_prof) {
+        cap_record(c);
+        return;
+    }
     cudaEventRecord(c->ev[c->ev_used].second, c->s);
     ++c->ev_used;
 }
@@ -365,7 +391,11 @@ void ucp_destroy(ucp_ctx* c)
         cudaEventDestroy(e.first);
         cudaEventDestroy(e.second);
     }
-    for (auto& g : c->graphs) cudaGraphExecDestroy(g.exec);
+    for (auto& g : c->graphs) {
+        cudaGraphExecDestroy(g.exec);
+        cudaGraphDestroy(g.graph);
+    }
+    for (cudaEvent_t e : c->cap_ev) cudaEventDestroy(e);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     delete c;
 }
@@ -740,7 +770,7 @@ static int run_block_graph(ucp_ctx* c, double dt_e, int kk, double theta, double
     for (auto& g : c->graphs)
         if (g.kk == kk && g.cur_in == c->cur && g.n_e == c->n_e &&
             g.n_chunks_all == c->n_chunks_all && g.n_chunks_e == c->n_chunks_e &&
-            g.dt_e == dt_e && g.theta == theta && g.eps == eps)
+            g.dt_e == dt_e && g.theta == theta && g.eps == eps && g.prof == c->prof)
             hit = &g;
     if (!hit) {
         if (!c->cap_stream && cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking))
@@ -756,7 +786,10 @@ static int run_block_graph(ucp_ctx* c, double dt_e, int kk, double theta, double
             c->s = orig;
             return fail(c, UCP_ECUDA, "begin capture");
         }
+        c->cap_prof = c->prof;
+        c->cap_ev_used = 0;
         rc = run_blocks(c, dt_e, kk, 1, theta, eps, nullptr);
+        c->cap_prof = false;
         cudaError_t ec = cudaStreamEndCapture(c->cap_stream, &graph);
         c->s = orig;
         const unsigned long long nl = g_launches.load() - l0;
@@ -771,13 +804,53 @@ static int run_block_graph(ucp_ctx* c, double dt_e, int kk, double theta, double
             cudaGetLastError();
             return rc ? rc : fail(c, UCP_ECUDA, "capture of a step block failed");
         }
+        // the event-record nodes, in the order their placeholder events were recorded
+        std::vector<cudaGraphNode_t> ev_nodes(c->prof ? c->cap_ev_used : 0, nullptr);
+        if (c->prof) {
+            size_t nn = 0;
+            cudaGraphGetNodes(graph, nullptr, &nn);
+            std::vector<cudaGraphNode_t> nodes(nn);
+            cudaGraphGetNodes(graph, nodes.data(), &nn);
+            for (cudaGraphNode_t nd : nodes) {
+                cudaGraphNodeType ty;
+                if (cudaGraphNodeGetType(nd, &ty) != cudaSuccess || ty != cudaGraphNodeTypeEventRecord)
+                    continue;
+                cudaEvent_t e;
+                if (cudaGraphEventRecordNodeGetEvent(nd, &e) != cudaSuccess) continue;
+                for (size_t i = 0; i < c->cap_ev_used; ++i)
+                    if (c->cap_ev[i] == e) ev_nodes[i] = nd;
+            }
+            for (cudaGraphNode_t nd : ev_nodes)
+                if (!nd || (ev_nodes.size() & 1)) {
+                    cudaGraphDestroy(graph);
+                    return fail(c, UCP_ECUDA, "profiled capture: event nodes not found");
+                }
+        }
         cudaGraphExec_t exec = nullptr;
         ec = cudaGraphInstantiate(&exec, graph, 0);
-        cudaGraphDestroy(graph);
-        if (ec != cudaSuccess) return fail(c, UCP_ECUDA, "graph instantiation failed");
+        if (ec != cudaSuccess) {
+            cudaGraphDestroy(graph);
+            return fail(c, UCP_ECUDA, "graph instantiation failed");
+        }
         c->graphs.push_back({kk, cur0, cur1, c->n_e, c->n_chunks_all, c->n_chunks_e, dt_e, theta,
-                             eps, exec, nl});
+                             eps, c->prof, graph, exec, nl, ev_nodes});
         hit = &c->graphs.back();
+    }
+    if (hit->prof) {
+        // point each walk's begin/end nodes at the next pair of the profiling pool
+        for (size_t i = 0; i + 1 < hit->ev_nodes.size(); i += 2) {
+            if (c->ev_used == c->ev.size()) {
+                cudaEvent_t a, b;
+                cudaEventCreate(&a);
+                cudaEventCreate(&b);
+                c->ev.push_back({a, b});
+            }
+            CK(cudaGraphExecEventRecordNodeSetEvent(hit->exec, hit->ev_nodes[i],
+                                                     c->ev[c->ev_used].first));
+            CK(cudaGraphExecEventRecordNodeSetEvent(hit->exec, hit->ev_nodes[i + 1],
+                                                     c->ev[c->ev_used].second));
+            ++c->ev_used;
+        }
     }
     CK(cudaGraphLaunch(hit->exec, c->s));
     count_launch((int)hit->launches);
@@ -845,7 +918,10 @@ int ucp_autotune(ucp_ctx* c, double theta, double eps, int* best_shape, float* b
     // the trial walks used this call's theta and eps: the next step recomputes
     // its first forces (identical to the cached ones when theta and eps agree)
     c->acc_valid = false;
-    for (auto& g : c->graphs) cudaGraphExecDestroy(g.exec);  // recapture with the new shape
+    for (auto& g : c->graphs) {  // recapture with the new shape
+        cudaGraphExecDestroy(g.exec);
+        cudaGraphDestroy(g.graph);
+    }
     c->graphs.clear();
     if (best_shape) *best_shape = best;
     if (best_ms) *best_ms = best_t / 2.f;
@@ -858,7 +934,10 @@ int ucp_set_walk_shape(ucp_ctx* c, int shape)
     if (shape < 0 || shape >= walk_shape_count() || walk_shape_count() != UCP_WALK_SHAPES)
         return fail(c, UCP_EINVAL, "walk shape out of range");
     if (c->walk_shape != shape) {
-        for (auto& g : c->graphs) cudaGraphExecDestroy(g.exec);
+        for (auto& g : c->graphs) {
+            cudaGraphExecDestroy(g.exec);
+            cudaGraphDestroy(g.graph);
+        }
         c->graphs.clear();
     }
     c->walk_shape = shape;
@@ -882,8 +961,7 @@ int ucp_step(ucp_ctx* c, double dt_e, int kk, int64_t n_electron_steps, double t
         return fail(c, UCP_EINVAL, "n_electron_steps must be a non-negative multiple of k");
     int rc = valid_walk_args(c, theta, eps);
     if (rc) return rc;
-    if (!c->use_graphs || c->prof) return run_blocks(c, dt_e, kk, n_electron_steps / kk, theta, eps,
-                                                     nullptr);
+    if (!c->use_graphs) return run_blocks(c, dt_e, kk, n_electron_steps / kk, theta, eps, nullptr);
     if (!c->acc_valid) {
         if (!c->tree_valid && (rc = build(c))) return rc;
         if ((rc = force(c, theta, eps, 0, false))) return rc;

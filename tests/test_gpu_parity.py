@@ -443,6 +443,25 @@ def test_graph_blocks_identical(U, prec, k):
     assert np.array_equal(res[0][3][:4], res[1][3][:4])
 
 
+def test_graph_blocks_profiled(U):
+    """Profiled replays: each walk of a replayed block is timed by event-record
+    nodes re-pointed at fresh events, and the trajectory is unchanged."""
+    c = gaussian_cloud(4096, 1.5, 63)
+    res = []
+    for graphs in (False, True):
+        with _ctx(U, c, 16, 1) as ctx:
+            ctx.set_graphs(graphs)
+            ctx.profile(True)
+            ctx.step(1e-3, 4, 12, 0.5, 0.01)     # 1 initial walk + 12 (3 blocks)
+            ms, n = ctx.profile_read()
+            ctx.step(1e-3, 4, 8, 0.5, 0.01)      # replays only: 8 walks
+            ms2, n2 = ctx.profile_read()
+            ctx.profile(False)
+            res.append(ctx.get_state())
+        assert n == 13 and n2 == 8 and ms > 0 and ms2 > 0
+    assert np.array_equal(res[0][0], res[1][0]) and np.array_equal(res[0][1], res[1][1])
+
+
 def test_graph_blocks_after_new_state(U):
     """A captured block is replayed only for launches it fits: a new state with a
     different electron count takes a new capture and matches a run without
