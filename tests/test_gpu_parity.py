@@ -480,6 +480,34 @@ def test_graph_blocks_after_new_state(U):
     assert np.array_equal(res[0][0], res[1][0]) and np.array_equal(res[0][1], res[1][1])
 
 
+def test_two_contexts_on_two_streams(U):
+    """Contexts are independent: two of them on two CUDA streams, their calls
+    interleaved, give what each gives alone."""
+    import torch
+    a = gaussian_cloud(3000, 1.4, 81)
+    b = gaussian_cloud(5000, 1.8, 82)
+    solo = []
+    for c in (a, b):
+        with _ctx(U, c, 16, 1) as ctx:
+            ctx.step(1e-3, 5, 10, 0.5, 0.01)
+            solo.append(ctx.get_state())
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    with torch.cuda.stream(s1):
+        ca = _ctx(U, a, 16, 1)
+    with torch.cuda.stream(s2):
+        cb = _ctx(U, b, 16, 1)
+    try:
+        for _ in range(2):
+            ca.step(1e-3, 5, 5, 0.5, 0.01)
+            cb.step(1e-3, 5, 5, 0.5, 0.01)
+        got = [ca.get_state(), cb.get_state()]
+    finally:
+        ca.close()
+        cb.close()
+    for (p0, v0), (p1, v1) in zip(solo, got):
+        assert np.array_equal(p0, p1) and np.array_equal(v0, v1)
+
+
 def test_graph_blocks_batch(U):
     from paper_0709_3331_gb300.inputs import batched_sizes
     sizes = [1024, 2048, 512]
