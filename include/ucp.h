@@ -138,6 +138,19 @@ int ucp_step(ucp_ctx* ctx, double dt_e, int ion_substep_ratio, int64_t n_electro
  * checkpoint_every) x 48 N bytes plus 96 bytes per box) and frees it before it
  * returns.  Plummer law only (UCP_EINVAL for Kelbg contexts).  Source-side
  * sums use atomic adds: gradients may differ between runs in the last bits. */
+/* The Hessian-vector walk on its own: mu = (d a / d x)^T lam for the TREE
+ * accelerations a (N x 3, = q E / m, Sec. 3 with the Eq. 5 criterion) at the
+ * current positions, the tree held fixed (the boxes a forward walk with theta
+ * accepts or opens), for a caller-order vector lam (N x 3); mu is N x 3 in caller
+ * order.  Pair and multipole terms are differentiated on both sides (targets,
+ * and sources through the box moments and centres), in FP64 (FP64 contexts) or
+ * the FP32 node-relative form (FP32C).  Allocates its working memory (72 bytes
+ * per particle plus 96 per box) and frees it before returning; synchronises the
+ * stream.  Plummer law only (UCP_EINVAL for Kelbg contexts); atomic source
+ * sums: results may differ between runs in the last bits. */
+int ucp_accel_vjp(ucp_ctx* ctx, double theta, double eps, const double* lam, double* mu,
+                  int on_device);
+
 int ucp_grad_ke_electrons(ucp_ctx* ctx, double dt_e, int ion_substep_ratio, int64_t n_steps,
                           double theta, double eps, int64_t checkpoint_every, double* loss,
                           double* grad_x, double* grad_v, int on_device);

@@ -1106,6 +1106,74 @@ int ucp_grad_ke_electrons(ucp_ctx* c, double dt_e, int kk, int64_t n_steps, doub
     return rc;
 }
 
+// (d a / d x)^T lam at the current positions, the tree held fixed: the adjoint
+// walk of the gradient call, on its own.
+int ucp_accel_vjp(ucp_ctx* c, double theta, double eps, const double* lam_in, double* mu_out,
+                  int on_device)
+{
+    if (!c || !lam_in || !mu_out) return UCP_EINVAL;
+    if (!c->have_state) return fail(c, UCP_ESTATE, "no state");
+    if (c->potential != UCP_POT_PLUMMER) return fail(c, UCP_EINVAL, "adjoint: Plummer law only");
+    int rc = valid_walk_args(c, theta, eps);
+    if (rc) return rc;
+    const size_t n3 = (size_t)3 * c->n;
+    double *lam = nullptr, *lsorted = nullptr, *mu = nullptr, *adj = nullptr, *out = nullptr;
+    auto freeall = [&]() {
+        for (double* p : {lam, lsorted, mu, adj, out})
+            if (p) cudaFree(p);
+    };
+    if (cudaMalloc(&lam, sizeof(double) * n3) || cudaMalloc(&lsorted, sizeof(double) * n3) ||
+        cudaMalloc(&mu, sizeof(double) * n3) || cudaMalloc(&out, sizeof(double) * n3) ||
+        cudaMalloc(&adj, sizeof(double) * (size_t)c->t.cap * 12)) {
+        cudaGetLastError();
+        freeall();
+        return fail(c, UCP_ENOMEM, "adjoint working memory");
+    }
+    cudaMemcpyKind kin = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    if (cudaMemcpyAsync(lam, lam_in, sizeof(double) * n3, kin, c->s) ||
+        cudaMemsetAsync(out, 0, sizeof(double) * n3, c->s)) {
+        freeall();
+        return fail(c, UCP_ECUDA, "adjoint input copy");
+    }
+    if (!c->tree_valid && (rc = build(c))) {
+        freeall();
+        return rc;
+    }
+    const int f32 = c->precision == UCP_FP32C;
+    launch_mac_prepare(c->t, c->cube, theta, f32, c->s);
+    const int k = c->cur;
+    launch_gather3(lam, c->id[k], c->n, lsorted, c->s);
+    WalkArgs a;
+    a.x = c->st[k][0];
+    a.y = c->st[k][1];
+    a.z = c->st[k][2];
+    a.sp = c->sp[k];
+    a.qsp = c->qsp;
+    a.msp = c->msp;
+    a.src32 = f32 ? c->src32 : nullptr;
+    a.t = c->t;
+    a.targets = nullptr;
+    a.ntargets = c->n;
+    a.chunks = c->chunks_all;
+    a.nchunks = c->n_chunks_all;
+    a.pos_off = c->pos_off;
+    a.eps2 = eps * eps;
+    a.kelbg = 0;
+    a.lambda = 1.0;
+    a.work = c->work;
+    a.err = c->sort.err;
+    launch_walk_adjoint(a, lsorted, mu, adj, c->t.cap, c->nsm, c->s);
+    launch_scatter_add3(mu, c->id[k], c->n, out, c->s);
+    rc = check_launch(c, "adjoint walk");
+    cudaMemcpyKind kout = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (!rc && cudaMemcpyAsync(mu_out, out, sizeof(double) * n3, kout, c->s))
+        rc = fail(c, UCP_ECUDA, "adjoint output copy");
+    cudaStreamSynchronize(c->s);
+    freeall();
+    if (!rc) rc = device_error(c);
+    return rc;
+}
+
 int ucp_energy(ucp_ctx* c, double theta, double eps, double out[6])
 {
     if (!c || !out) return UCP_EINVAL;

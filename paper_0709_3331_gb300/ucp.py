@@ -31,7 +31,7 @@ EXPORTS = ("ucp_create", "ucp_destroy", "ucp_set_state", "ucp_get_state", "ucp_t
            "ucp_get_sorted", "ucp_get_tree", "ucp_get_counts", "ucp_profile", "ucp_profile_read",
            "ucp_strerror", "ucp_last_error", "ucp_selftest_wait_timeout", "ucp_create_batch",
            "ucp_energy_clouds", "ucp_get_cubes", "ucp_grad_ke_electrons", "ucp_set_graphs",
-           "ucp_autotune", "ucp_set_walk_shape", "ucp_measure_peaks")
+           "ucp_autotune", "ucp_set_walk_shape", "ucp_measure_peaks", "ucp_accel_vjp")
 
 
 class UcpError(RuntimeError):
@@ -84,6 +84,8 @@ def lib():
         L.ucp_grad_ke_electrons.restype = C.c_int
         L.ucp_autotune.argtypes = [vp, dbl, dbl, C.POINTER(i32), C.POINTER(C.c_float)]
         L.ucp_autotune.restype = C.c_int
+        L.ucp_accel_vjp.argtypes = [vp, dbl, dbl, vp, vp, i32]
+        L.ucp_accel_vjp.restype = C.c_int
         L.ucp_measure_peaks.argtypes = [C.POINTER(C.c_double), vp]
         L.ucp_measure_peaks.restype = C.c_int
         L.ucp_set_walk_shape.argtypes = [vp, i32]
@@ -238,6 +240,21 @@ class Context:
         self._check(lib().ucp_energy(self._h, float(theta), float(eps), out.ctypes.data),
                     "ucp_energy")
         return out
+
+    def accel_vjp(self, theta, eps, lam, mu=None):
+        """mu = (d a / d x)^T lam at the current positions, tree held fixed
+        (``ucp_accel_vjp``); lam and mu are N x 3 in caller order (numpy or
+        torch CUDA tensors)."""
+        if mu is None:
+            mu = (np.zeros((self.n, 3)) if not _is_torch(lam)
+                  else lam.new_zeros((self.n, 3)))
+        lp, ld = _ptr(lam, np.float64)
+        mp, md = _ptr(mu, np.float64)
+        if ld != md:
+            raise TypeError("lam and mu must both be host or both be device arrays")
+        self._check(lib().ucp_accel_vjp(self._h, float(theta), float(eps), lp, mp, ld),
+                    "ucp_accel_vjp")
+        return mu
 
     def grad_ke_electrons(self, dt_e, ion_substep_ratio, n_steps, theta, eps,
                           checkpoint_every=None, grad_x=None, grad_v=None):

@@ -99,3 +99,54 @@ def test_autograd_front_end(U):
     # two runs of the gradient: the source-side atomic sums may differ in the last bits
     gxa, gva = pos.grad.cpu().numpy(), vel.grad.cpu().numpy()
     assert rel_rms(gxa, 2.0 * gx) <= 1e-5 and rel_rms(gva, 2.0 * gv) <= 1e-5
+
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-6), (1, 1e-4)])
+@pytest.mark.parametrize("theta", [0.5, 0.9])
+def test_accel_vjp_vs_oracle(U, orc, prec, tol, theta):
+    """ucp_accel_vjp against the oracle's frozen-tree adjoint of the accelerations."""
+    c = gaussian_cloud(2048, 1.0, 3)
+    lam = np.random.default_rng(5).standard_normal((c.n, 3))
+    mu_ref = orc.force_adjoint(c.pos, c.species, c.q, c.m, lam, theta, 0.01, leaf_cap=8)
+    with U.Context(c.n, c.q, c.m, leaf_cap=8, precision=prec) as ctx:
+        ctx.set_state(c.pos, c.vel, c.species)
+        mu = ctx.accel_vjp(theta, 0.01, lam)
+    assert rel_rms(mu, mu_ref) <= tol
+
+
+def test_accel_vjp_direct_sum_finite_differences(U):
+    """At theta = 0 the walk is the direct sum, smooth in the positions: the
+    vector-Jacobian product matches central differences of lam . a."""
+    c = gaussian_cloud(512, 1.0, 9)
+    lam = np.random.default_rng(6).standard_normal((c.n, 3))
+    eps, h = 0.05, 1e-5
+    with U.Context(c.n, c.q, c.m, leaf_cap=8, precision=0) as ctx:
+        ctx.set_state(c.pos, c.vel, c.species)
+        mu = ctx.accel_vjp(0.0, eps, lam)
+        rng = np.random.default_rng(7)
+        for _ in range(12):
+            i, d = int(rng.integers(c.n)), int(rng.integers(3))
+            vals = []
+            for sgn in (1.0, -1.0):
+                p = c.pos.copy()
+                p[i, d] += sgn * h
+                ctx.set_state(p, c.vel, c.species)
+                a, _ = ctx.tree_force(0.0, eps)
+                vals.append((lam * a).sum())
+            fd = (vals[0] - vals[1]) / (2 * h)
+            assert fd == pytest.approx(mu[i, d], rel=1e-4, abs=1e-6 * np.abs(mu).max())
+
+
+def test_accel_vjp_device_arrays(U):
+    import torch
+    c = gaussian_cloud(1000, 1.0, 4)
+    lam = np.random.default_rng(8).standard_normal((c.n, 3))
+    with U.Context(c.n, c.q, c.m, leaf_cap=8, precision=1) as ctx:
+        ctx.set_state(c.pos, c.vel, c.species)
+        mu_h = ctx.accel_vjp(0.5, 0.01, lam)
+        mu_d = ctx.accel_vjp(0.5, 0.01, torch.from_numpy(lam).cuda()).cpu().numpy()
+    with U.Context(4, kelbg_lambda=0.1) as ck:
+        ck.set_state(c.pos[:4].copy(), c.vel[:4].copy(), c.species[:4].copy())
+        with pytest.raises(U.UcpError):          # the Kelbg law has no adjoint here
+            ck.accel_vjp(0.5, 0.01, np.zeros((4, 3)))
+    assert rel_rms(mu_d, mu_h) <= 1e-6
