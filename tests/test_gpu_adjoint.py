@@ -150,3 +150,24 @@ def test_accel_vjp_device_arrays(U):
         with pytest.raises(U.UcpError):          # the Kelbg law has no adjoint here
             ck.accel_vjp(0.5, 0.01, np.zeros((4, 3)))
     assert rel_rms(mu_d, mu_h) <= 1e-6
+
+
+def test_tree_accel_autograd(U):
+    """tree_accel is differentiable in the positions: its backward equals
+    ucp_accel_vjp, and at theta = 0 (the direct sum) torch.autograd.gradcheck
+    passes against finite differences."""
+    import torch
+    from paper_0709_3331_gb300.autograd import tree_accel
+    dev = torch.device("cuda")
+    c = gaussian_cloud(64, 1.0, 12)
+    sp = torch.from_numpy(c.species).to(dev)
+    with U.Context(c.n, c.q, c.m, leaf_cap=4, precision=0) as ctx:
+        pos = torch.from_numpy(c.pos).to(dev).requires_grad_(True)
+        w = torch.from_numpy(np.random.default_rng(3).standard_normal((c.n, 3))).to(dev)
+        (tree_accel(pos, sp, ctx, 0.5, 0.01) * w).sum().backward()
+        ctx.set_state(c.pos, c.vel, c.species)
+        mu = ctx.accel_vjp(0.5, 0.01, w.cpu().numpy())
+        assert rel_rms(pos.grad.cpu().numpy(), mu) <= 1e-12
+        p0 = torch.from_numpy(c.pos).to(dev).requires_grad_(True)
+        assert torch.autograd.gradcheck(lambda x: tree_accel(x, sp, ctx, 0.0, 0.05), (p0,),
+                                        eps=1e-6, atol=1e-6, rtol=1e-4)
