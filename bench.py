@@ -364,7 +364,7 @@ def run_gpu(args):
                    "walk_shape": {"index": shape, "threads": WALK_SHAPE_TABLE[shape][0],
                                   "blocks_per_sm": WALK_SHAPE_TABLE[shape][1],
                                   "staged_leaf_sources": bool(WALK_SHAPE_TABLE[shape][2]),
-                                  "autotune_ms_per_walk": shape_ms}},
+                                  "autotune_ms_walks_per_block": shape_ms}},
         "particle_steps_per_s": pst,
         "p2p_pairs_per_s": float(st[0]) * ws / (ms_all / 1e3),
         "m2p_evals_per_s": float(st[1]) * ws / (ms_all / 1e3),
@@ -477,6 +477,20 @@ def run_extras(c, W, ws, pos_d, vel_d, sp_d, Context, UCP_FP32C, UCP_FP64, timed
                           "walk_frac_fp32_peak": fl / (wm / 1e3) / 1e12 / peak}
         cs.close()
     extra["theta_sweep"] = sweep
+
+    # the Kelbg electron-ion law (Sec. 2.1 Eq. 3, lambda_ei = 0.05 in these units)
+    # on the same workload: one block, FP32C
+    ck = Context(c.n, c.q, c.m, leaf_cap=W["leaf_cap"], precision=UCP_FP32C, kelbg_lambda=0.05)
+    ck.set_state(pos_d, vel_d, sp_d)
+    ck.step(W["dt_e"], W["k"], W["k"], W["theta"], W["eps"])
+    torch.cuda.synchronize()
+    mk, stk, wmk, wnk, _ = timed_steps(ck, 2, energy=False)
+    extra["kelbg_fp32c"] = {
+        "lambda_ei": 0.05, "ms_per_step": mk / 2,
+        "interactions_per_s": float(stk[0] + stk[1]) / (mk / 1e3),
+        "walk_ms_per_launch": wmk / max(wnk, 1),
+        "note": "electron-ion direct pairs take the Kelbg form one source at a time"}
+    ck.close()
 
     # ensemble of 64 independent clouds (sizes log-uniform 4096..65536, sigma_c =
     # (N_c/2048)^(1/3)) in one context: every stage one launch for all clouds

@@ -163,11 +163,13 @@ int ucp_grad_ke_electrons(ucp_ctx* ctx, double dt_e, int ion_substep_ratio, int6
  * (small clouds, ensembles). */
 int ucp_set_graphs(ucp_ctx* ctx, int enable);
 
-/* Autotuner of the FP32C walk: times one walk over every particle of the current
- * state in each launch shape the library has (threads per block x resident blocks
- * per SM of the persistent walk) and keeps the fastest for this context (returned
- * in *best_shape, its time in *best_ms; either may be NULL).  Results do not
- * depend on the shape.  FP64 contexts keep their single shape. */
+/* Autotuner of the FP32C walk: times, in each launch shape the library has
+ * (threads per block x resident blocks per SM, sources through L1 or staged in
+ * shared memory), the walks of one block of 10 electron substeps on the current
+ * state (one walk over every particle and nine over the electrons; best of three
+ * after a warm-up) and keeps the fastest shape for this context (returned in
+ * *best_shape, that block's walk time in ms in *best_ms; either may be NULL).
+ * Results do not depend on the shape.  FP64 contexts keep their single shape. */
 int ucp_autotune(ucp_ctx* ctx, double theta, double eps, int* best_shape, float* best_ms);
 
 /* Number of FP32C walk launch shapes, and a call that sets one directly

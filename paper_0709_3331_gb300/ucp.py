@@ -331,7 +331,7 @@ class Context:
 
     def autotune(self, theta, eps):
         """Pick the fastest launch shape of the FP32C walk on the current state;
-        returns (shape index, ms per walk)."""
+        returns (shape index, ms for the walks of one 10-substep block)."""
         sh = C.c_int(0)
         ms = C.c_float(0.0)
         self._check(lib().ucp_autotune(self._h, float(theta), float(eps), C.byref(sh),
