@@ -2,7 +2,8 @@
 profiler to capture (``ncu ... python -m paper_0709_3331_gb300.profile_case``).
 
 ``--what force`` runs ``ucp_tree_force`` (build + one walk over every
-particle); ``--what step`` runs ``ucp_step`` blocks.
+particle); ``--what step`` runs ``ucp_step`` blocks; ``--what grad`` runs
+``ucp_grad_ke_electrons`` over one block (checkpoint at its end).
 """
 from __future__ import annotations
 
@@ -22,7 +23,7 @@ def main():
     ap.add_argument("--theta", type=float, default=0.5)
     ap.add_argument("--eps", type=float, default=0.01)
     ap.add_argument("--leaf-cap", type=int, default=16)
-    ap.add_argument("--what", default="force", choices=["force", "step"])
+    ap.add_argument("--what", default="force", choices=["force", "step", "grad"])
     ap.add_argument("--repeat", type=int, default=1)
     ap.add_argument("--shape", type=int, default=0, help="FP32C walk launch shape")
     a = ap.parse_args()
@@ -42,6 +43,10 @@ def main():
     for _ in range(a.repeat):
         if a.what == "force":
             ctx.tree_force(a.theta, a.eps, acc, phi)
+        elif a.what == "grad":
+            gx = torch.empty((c.n, 3), dtype=torch.float64, device=dev)
+            gv = torch.empty_like(gx)
+            ctx.grad_ke_electrons(1e-3, 10, 10, a.theta, a.eps, 10, gx, gv)
         else:
             ctx.step(1e-3, 10, 10, a.theta, a.eps)
     torch.cuda.synchronize()
