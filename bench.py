@@ -442,6 +442,8 @@ def run_extras(c, W, ws, pos_d, vel_d, sp_d, Context, UCP_FP32C, UCP_FP64, timed
     extra = {}
     ctx64 = Context(c.n, c.q, c.m, leaf_cap=W["leaf_cap"], precision=UCP_FP64)
     ctx64.set_state(pos_d, vel_d, sp_d)
+    ctx64.set_graphs(True)     # like the headline: blocks replay a profiled capture
+    ctx64.profile(True)
     ctx64.step(W["dt_e"], W["k"], W["k"], W["theta"], W["eps"])
     torch.cuda.synchronize()
     ms64, st64, wms64, wn64, _ = timed_steps(ctx64, 1)
@@ -453,6 +455,8 @@ def run_extras(c, W, ws, pos_d, vel_d, sp_d, Context, UCP_FP32C, UCP_FP64, timed
     for th in (0.3, 0.5, 0.7):
         cs = Context(c.n, c.q, c.m, leaf_cap=W["leaf_cap"], precision=UCP_FP32C)
         cs.set_state(pos_d, vel_d, sp_d)
+        cs.set_graphs(True)
+        cs.profile(True)
         cs.step(W["dt_e"], W["k"], W["k"], th, W["eps"])
         torch.cuda.synchronize()
         cs.stats(reset=True)
@@ -482,6 +486,8 @@ def run_extras(c, W, ws, pos_d, vel_d, sp_d, Context, UCP_FP32C, UCP_FP64, timed
     # on the same workload: one block, FP32C
     ck = Context(c.n, c.q, c.m, leaf_cap=W["leaf_cap"], precision=UCP_FP32C, kelbg_lambda=0.05)
     ck.set_state(pos_d, vel_d, sp_d)
+    ck.set_graphs(True)
+    ck.profile(True)
     ck.step(W["dt_e"], W["k"], W["k"], W["theta"], W["eps"])
     torch.cuda.synchronize()
     mk, stk, wmk, wnk, _ = timed_steps(ck, 2, energy=False)
