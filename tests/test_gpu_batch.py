@@ -132,3 +132,30 @@ def test_batch_rejects_bad_sizes(U):
         U.Context(11, sizes=[5, 5])
     with pytest.raises(U.UcpError):
         U.Context(300, sizes=[1] * 300)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_batch_kelbg_equals_solo(U, prec):
+    """The Kelbg electron-ion law in an ensemble: every cloud as alone, and the
+    same when the blocks replay captured graphs."""
+    sizes = [2000, 700, 3000]
+    clouds, pos, vel, sp = _ensemble(sizes, seed0=31)
+    c0 = clouds[0]
+    with U.Context(len(sp), c0.q, c0.m, leaf_cap=16, precision=prec, sizes=sizes,
+                   kelbg_lambda=0.05) as ctx:
+        ctx.set_graphs(True)
+        ctx.set_state(pos, vel, sp)
+        acc, phi = ctx.tree_force(0.5, 0.01)
+        ctx.step(1e-3, 5, 10, 0.5, 0.01)
+        p, v = ctx.get_state()
+    off = 0
+    for c in clouds:
+        with U.Context(c.n, c.q, c.m, leaf_cap=16, precision=prec, kelbg_lambda=0.05) as solo:
+            solo.set_state(c.pos, c.vel, c.species)
+            a1, p1 = solo.tree_force(0.5, 0.01)
+            solo.step(1e-3, 5, 10, 0.5, 0.01)
+            q1, w1 = solo.get_state()
+        sl = slice(off, off + c.n)
+        assert np.array_equal(acc[sl], a1) and np.array_equal(phi[sl], p1)
+        assert np.array_equal(p[sl], q1) and np.array_equal(v[sl], w1)
+        off += c.n
