@@ -159,3 +159,25 @@ def test_batch_kelbg_equals_solo(U, prec):
         assert np.array_equal(acc[sl], a1) and np.array_equal(phi[sl], p1)
         assert np.array_equal(p[sl], q1) and np.array_equal(v[sl], w1)
         off += c.n
+
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-12), (1, 1e-6)])
+def test_batch_accel_vjp_equals_solo(U, prec, tol):
+    """The frozen-tree adjoint walk on an ensemble gives each cloud's own
+    vector-Jacobian product (the source-side atomic sums may differ in the last
+    bits, so within rounding)."""
+    sizes = [1500, 400, 2600]
+    clouds, pos, vel, sp = _ensemble(sizes, seed0=41)
+    lam = np.random.default_rng(2).standard_normal((len(sp), 3))
+    c0 = clouds[0]
+    with U.Context(len(sp), c0.q, c0.m, leaf_cap=16, precision=prec, sizes=sizes) as ctx:
+        ctx.set_state(pos, vel, sp)
+        mu = ctx.accel_vjp(0.5, 0.01, lam)
+    off = 0
+    for c in clouds:
+        sl = slice(off, off + c.n)
+        with U.Context(c.n, c.q, c.m, leaf_cap=16, precision=prec) as solo:
+            solo.set_state(c.pos, c.vel, c.species)
+            m1 = solo.accel_vjp(0.5, 0.01, lam[sl].copy())
+        assert rel_rms(mu[sl], m1) <= tol
+        off += c.n
