@@ -181,3 +181,24 @@ def test_batch_accel_vjp_equals_solo(U, prec, tol):
             m1 = solo.accel_vjp(0.5, 0.01, lam[sl].copy())
         assert rel_rms(mu[sl], m1) <= tol
         off += c.n
+
+
+def test_batch_gradient_equals_solo(U):
+    """ucp_grad_ke_electrons on an ensemble: the loss is the sum of the clouds'
+    losses and each cloud's gradient is its own (within the atomic-sum rounding)."""
+    sizes = [1200, 900]
+    clouds, pos, vel, sp = _ensemble(sizes, seed0=51)
+    c0 = clouds[0]
+    with U.Context(len(sp), c0.q, c0.m, leaf_cap=16, precision=1, sizes=sizes) as ctx:
+        ctx.set_state(pos, vel, sp)
+        L, gx, gv = ctx.grad_ke_electrons(1e-3, 2, 6, 0.5, 0.01, 2)
+    off, Ls = 0, 0.0
+    for c in clouds:
+        sl = slice(off, off + c.n)
+        with U.Context(c.n, c.q, c.m, leaf_cap=16, precision=1) as solo:
+            solo.set_state(c.pos, c.vel, c.species)
+            L1, gx1, gv1 = solo.grad_ke_electrons(1e-3, 2, 6, 0.5, 0.01, 2)
+        Ls += L1
+        assert rel_rms(gx[sl], gx1) <= 1e-6 and rel_rms(gv[sl], gv1) <= 1e-6
+        off += c.n
+    assert L == pytest.approx(Ls, rel=1e-12)
