@@ -27,12 +27,14 @@ def _walk(ctx, theta, eps):
     return acc, phi, p2p, m2p
 
 
-@pytest.mark.parametrize("sizes", [None, [3000, 517, 20000, 33]])
-def test_every_shape_same_forces(U, sizes):
+@pytest.mark.parametrize("sizes,lam", [(None, None), ([3000, 517, 20000, 33], None),
+                                       (None, 0.05)])
+def test_every_shape_same_forces(U, sizes, lam):
     from paper_0709_3331_gb300.ucp import UCP_WALK_SHAPES
     n = 20000 if sizes is None else sum(sizes)
     c = gaussian_cloud(n, 3.0, 41)
-    with U.Context(n, c.q, c.m, leaf_cap=16, precision=1, sizes=sizes) as ctx:
+    with U.Context(n, c.q, c.m, leaf_cap=16, precision=1, sizes=sizes,
+                   kelbg_lambda=lam) as ctx:
         ctx.set_state(c.pos, c.vel, c.species)
         ref = _walk(ctx, 0.5, 0.01)
         for sh in range(1, UCP_WALK_SHAPES):
