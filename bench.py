@@ -627,6 +627,45 @@ def run_extras(c, W, ws, pos_d, vel_d, sp_d, Context, UCP_FP32C, UCP_FP64, timed
     return extra
 
 
+def run_profile_case(args):
+    """One named case through the C ABI, a fixed number of times, for a profiler
+    to capture (no timing, no JSON line).  ``force``: tree build + one walk over
+    every particle; ``step``: blocks of 10 electron substeps; ``grad``: the
+    gradient over one block (checkpoint at its end)."""
+    import torch
+
+    from paper_0709_3331_gb300 import UCP_FP32C, UCP_FP64, Context
+    from paper_0709_3331_gb300.inputs import WORKLOADS, gaussian_cloud
+
+    w = dict(WORKLOADS[args.workload])
+    if args.n:
+        w["n"] = args.n
+    c = gaussian_cloud(**w)
+    dev = torch.device("cuda")
+    prec = UCP_FP32C if args.precision == "fp32c" else UCP_FP64
+    ctx = Context(c.n, c.q, c.m, leaf_cap=args.leaf_cap, precision=prec)
+    ctx.set_state(torch.from_numpy(c.pos).to(dev), torch.from_numpy(c.vel).to(dev),
+                  torch.from_numpy(c.species).to(dev))
+    if prec == UCP_FP32C:
+        ctx.set_walk_shape(args.shape)
+    acc = torch.empty((c.n, 3), dtype=torch.float64, device=dev)
+    phi = torch.empty(c.n, dtype=torch.float64, device=dev)
+    for _ in range(args.repeat):
+        if args.profile_case == "force":
+            ctx.tree_force(args.theta, 0.01, acc, phi)
+        elif args.profile_case == "grad":
+            gx = torch.empty((c.n, 3), dtype=torch.float64, device=dev)
+            gv = torch.empty_like(gx)
+            ctx.grad_ke_electrons(1e-3, 10, 10, args.theta, 0.01, 10, gx, gv)
+        else:
+            ctx.step(1e-3, 10, 10, args.theta, 0.01)
+    torch.cuda.synchronize()
+    st = ctx.stats()
+    print(f"n={c.n} walks={st[3]} p2p={st[0]} m2p={st[1]} boxes={st[4]} depth={st[5]}")
+    ctx.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -636,7 +675,18 @@ def main():
     ap.add_argument("--quick", action="store_true", help="skip the FP64 and theta-sweep lines")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer e2e leg")
+    # a single untimed case for a profiler (see run_profile_case)
+    ap.add_argument("--profile-case", choices=["force", "step", "grad"], default=None)
+    ap.add_argument("--workload", default="precision_n524288")
+    ap.add_argument("--n", type=int, default=0, help="profile case: override the particle count")
+    ap.add_argument("--precision", default="fp32c", choices=["fp32c", "fp64"])
+    ap.add_argument("--theta", type=float, default=0.5)
+    ap.add_argument("--leaf-cap", type=int, default=16)
+    ap.add_argument("--repeat", type=int, default=1)
+    ap.add_argument("--shape", type=int, default=0, help="profile case: FP32C walk launch shape")
     args = ap.parse_args()
+    if args.profile_case:
+        return run_profile_case(args)
     if args.warmup < 3 and args.impl == "gpu":
         args.warmup = 3
     if args.impl == "reference":
