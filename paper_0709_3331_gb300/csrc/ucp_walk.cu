@@ -120,7 +120,8 @@ __device__ __forceinline__ void m2p<double>(double rx, double ry, double rz, dou
     ez += aa * rz - g3 * (Dz + s3 * QRz);
 }
 
-// FP32 form; T = -tr(Q)/2 comes with the box record
+// FP32 form; T = -tr(Q)/2 comes with the box record.  kPhi = false: field only.
+template <bool kPhi>
 __device__ __forceinline__ void m2p_f32(float rx, float ry, float rz, float r2, float T, float M,
                                         float Dx, float Dy, float Dz, float Qxx, float Qxy,
                                         float Qxz, float Qyy, float Qyz, float Qzz, float& ex,
@@ -135,7 +136,7 @@ __device__ __forceinline__ void m2p_f32(float rx, float ry, float rz, float r2, 
     float RQR = fmaf(rx, QRx, fmaf(ry, QRy, rz * QRz));
     float w = fmaf(Dx, rx, fmaf(Dy, ry, fmaf(Dz, rz, T)));
     float h = u * RQR;
-    ph = fmaf(g, fmaf(u, fmaf(1.5f, h, w), M), ph);
+    if (kPhi) ph = fmaf(g, fmaf(u, fmaf(1.5f, h, w), M), ph);
     float s3 = 3.f * u;
     float aa = g3 * fmaf(s3, fmaf(2.5f, h, w), M);
     float mg3 = -g3;
@@ -309,7 +310,10 @@ __device__ __forceinline__ void kelbg_pg(float u, float& p, float& g)
 // kStage: a leaf's sources (up to 32) are brought into shared memory by a bulk
 // copy issued one list entry ahead (double buffer per warp) instead of being read
 // through L1 by every lane; the arithmetic and its order are the same.
-template <bool kKelbg, int kThreads, int kBlocks, bool kStage>
+// kPhi = false (walks whose potential nobody reads, e.g. the electron substeps):
+// the potential terms and their sums are left out; the field is computed by the
+// same operations in the same order, so accelerations are bit-identical.
+template <bool kKelbg, int kThreads, int kBlocks, bool kStage, bool kPhi>
 __global__ void __launch_bounds__(kThreads, kBlocks)
 k_walk_fp32c(WalkArgs a)
 {
@@ -365,7 +369,7 @@ k_walk_fp32c(WalkArgs a)
             two_sum_acc(sx, cx, bx);
             two_sum_acc(sy, cy, by);
             two_sum_acc(sz, cz, bz);
-            two_sum_acc(sp, cp, bp);
+            if (kPhi) two_sum_acc(sp, cp, bp);
             bx = by = bz = bp = 0.f;
         };
 
@@ -396,13 +400,13 @@ k_walk_fp32c(WalkArgs a)
                 px = __ffma2_rn(qr3, dx, px);
                 py = __ffma2_rn(qr3, dy, py);
                 pz = __ffma2_rn(qr3, dz, pz);
-                pp = __fadd2_rn(pp, qi);
+                if (kPhi) pp = __fadd2_rn(pp, qi);
             }
             np += (je - jb) - ((t >= jb && t < je) ? 1 : 0);
             two_sum_acc(sx, cx, px.x + px.y);
             two_sum_acc(sy, cy, py.x + py.y);
             two_sum_acc(sz, cz, pz.x + pz.y);
-            two_sum_acc(sp, cp, pp.x + pp.y);
+            if (kPhi) two_sum_acc(sp, cp, pp.x + pp.y);
         };
 
         // Staged form: entry e's sources go to buffer e & 1 while entry e - 1 is
@@ -533,13 +537,13 @@ k_walk_fp32c(WalkArgs a)
                         px = __ffma2_rn(qr3, dx, px);
                         py = __ffma2_rn(qr3, dy, py);
                         pz = __ffma2_rn(qr3, dz, pz);
-                        pp = __fadd2_rn(pp, qi);
+                        if (kPhi) pp = __fadd2_rn(pp, qi);
                     }
                     np += (je - jb) - ((t >= jb && t < je) ? 1 : 0);
                     two_sum_acc(sx, cx, px.x + px.y);
                     two_sum_acc(sy, cy, py.x + py.y);
                     two_sum_acc(sz, cz, pz.x + pz.y);
-                    two_sum_acc(sp, cp, pp.x + pp.y);
+                    if (kPhi) two_sum_acc(sp, cp, pp.x + pp.y);
                 }
             }
             npl = 0;
@@ -588,7 +592,7 @@ k_walk_fp32c(WalkArgs a)
                 }
             }
             if (acc) {
-                m2p_f32(rx, ry, rz, d2 + eps2, C.x, C.z, C.w, D.x, D.y, D.z, D.w, E.x, E.y, E.z,
+                m2p_f32<kPhi>(rx, ry, rz, d2 + eps2, C.x, C.z, C.w, D.x, D.y, D.z, D.w, E.x, E.y, E.z,
                         E.w, bx, by, bz, bp);
                 ++nm;
             }
@@ -605,7 +609,7 @@ k_walk_fp32c(WalkArgs a)
             a.ax[t] = qm * ((double)sx + (double)cx);
             a.ay[t] = qm * ((double)sy + (double)cy);
             a.az[t] = qm * ((double)sz + (double)cz);
-            if (a.phi) a.phi[t] = (double)sp + (double)cp;
+            if (kPhi && a.phi) a.phi[t] = (double)sp + (double)cp;
             a.cnt_p2p[t] = np;
             a.cnt_m2p[t] = nm;
         }
@@ -715,16 +719,16 @@ static const int kShapes[][3] = {{128, 7, 0}, {896, 1, 0}, {128, 8, 0}, {1024, 1
                                  {128, 8, 1}, {256, 4, 1}};
 int walk_shape_count() { return (int)(sizeof(kShapes) / sizeof(kShapes[0])); }
 
-template <bool kKelbg, bool kStage>
+template <bool kKelbg, bool kStage, bool kPhi>
 static void walk_fp32c_shape(const WalkArgs& a, int th, int per_sm, int b, cudaStream_t s)
 {
-    if (th == 32) k_walk_fp32c<kKelbg, 32, 24, false><<<b, 32, 0, s>>>(a);
-    else if (th == 896) k_walk_fp32c<kKelbg, 896, 1, kStage><<<b, 896, 0, s>>>(a);
-    else if (th == 1024) k_walk_fp32c<kKelbg, 1024, 1, false><<<b, 1024, 0, s>>>(a);
-    else if (th == 256) k_walk_fp32c<kKelbg, 256, 4, kStage><<<b, 256, 0, s>>>(a);
-    else if (th == 512) k_walk_fp32c<kKelbg, 512, 2, false><<<b, 512, 0, s>>>(a);
-    else if (per_sm >= 8) k_walk_fp32c<kKelbg, 128, 8, kStage><<<b, 128, 0, s>>>(a);
-    else k_walk_fp32c<kKelbg, 128, 7, kStage><<<b, 128, 0, s>>>(a);
+    if (th == 32) k_walk_fp32c<kKelbg, 32, 24, false, kPhi><<<b, 32, 0, s>>>(a);
+    else if (th == 896) k_walk_fp32c<kKelbg, 896, 1, kStage, kPhi><<<b, 896, 0, s>>>(a);
+    else if (th == 1024) k_walk_fp32c<kKelbg, 1024, 1, false, kPhi><<<b, 1024, 0, s>>>(a);
+    else if (th == 256) k_walk_fp32c<kKelbg, 256, 4, kStage, kPhi><<<b, 256, 0, s>>>(a);
+    else if (th == 512) k_walk_fp32c<kKelbg, 512, 2, false, kPhi><<<b, 512, 0, s>>>(a);
+    else if (per_sm >= 8) k_walk_fp32c<kKelbg, 128, 8, kStage, kPhi><<<b, 128, 0, s>>>(a);
+    else k_walk_fp32c<kKelbg, 128, 7, kStage, kPhi><<<b, 128, 0, s>>>(a);
 }
 
 void launch_walk_fp32c(const WalkArgs& a, int nsm, cudaStream_t s, int shape)
@@ -737,9 +741,14 @@ void launch_walk_fp32c(const WalkArgs& a, int nsm, cudaStream_t s, int shape)
     // the Kelbg pair law reads its sources directly
     const bool stage = kShapes[shape][2] != 0 && !a.kelbg;
     walk_grid(a.nchunks, nsm, &th, per_sm, &b);
-    if (a.kelbg) walk_fp32c_shape<true, false>(a, th, per_sm, b, s);
-    else if (stage) walk_fp32c_shape<false, true>(a, th, per_sm, b, s);
-    else walk_fp32c_shape<false, false>(a, th, per_sm, b, s);
+    // the potential is computed only when the caller reads it (the Kelbg form
+    // always computes it)
+    const bool phi = a.phi != nullptr;
+    if (a.kelbg) walk_fp32c_shape<true, false, true>(a, th, per_sm, b, s);
+    else if (stage && phi) walk_fp32c_shape<false, true, true>(a, th, per_sm, b, s);
+    else if (stage) walk_fp32c_shape<false, true, false>(a, th, per_sm, b, s);
+    else if (phi) walk_fp32c_shape<false, false, true>(a, th, per_sm, b, s);
+    else walk_fp32c_shape<false, false, false>(a, th, per_sm, b, s);
 }
 
 }  // namespace ucp
