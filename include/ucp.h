@@ -252,11 +252,16 @@ int ucp_measure_peaks(double out[4], void* stream);
  * (cudaStream_t, NULL = legacy stream); it returns after enqueueing.
  * It calls no cudaMalloc or cudaFree: its per-tile partial results live in a
  * fixed array in the library's device memory (UCP_STATIC_MAX_N /
- * UCP_STATIC_TILE slots of 6 doubles, 48 KB, present on every GPU that loads
- * the library until the process exits).  N outside [1, UCP_STATIC_MAX_N]
- * returns UCP_EINVAL; a failed CUDA call returns UCP_ECUDA.
- * The first call on a device looks up that array's device address (once per
- * device, with that device current); make that first call before any stream
+ * UCP_STATIC_TILE slots of 6 64-bit words, 48 KB, present on every GPU that
+ * loads the library until the process exits).  N outside [1, UCP_STATIC_MAX_N]
+ * returns UCP_EINVAL; a failed CUDA call returns UCP_ECUDA.  Min and max are
+ * taken exactly as ucp_tree_build takes them, so the two cubes agree bit for
+ * bit, signed zeros included; a NaN coordinate (which ucp_set_state refuses)
+ * makes that axis's centre NaN here.
+ * The first call on a device looks up that array's device address, with that
+ * device current, and keeps it with the CUDA context it belongs to; a call in
+ * another context (after a device reset, say) looks it up again.  Make the
+ * first call on each device, and the first after a reset, before any stream
  * capture.  All calls share the one array and each call overwrites the slots
  * it uses, so calls that may run at the same time on the GPU (different
  * streams without ordering between them) race and must be serialised. */

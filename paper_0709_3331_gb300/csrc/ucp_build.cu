@@ -104,16 +104,6 @@ __global__ void k_scan_apply(const int* __restrict__ in, int* __restrict__ out, 
 // ---------------------------------------------------------------- cube
 // Ordered integer image of a finite double: comparing the images compares the
 // values, so min/max run on the integer ALU instead of the (scarce) FP64 pipe.
-__device__ __forceinline__ unsigned long long ord64(double v)
-{
-    unsigned long long b = (unsigned long long)__double_as_longlong(v);
-    return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
-}
-__device__ __forceinline__ double unord64(unsigned long long u)
-{
-    return __longlong_as_double((long long)((u >> 63) ? (u & 0x7fffffffffffffffull) : ~u));
-}
-
 // Partial min/max of cloud blockIdx.y over its segment (the whole array when
 // cloud_start is NULL); block x of the cloud strides the segment.
 __global__ void k_bbox_partial(const double* __restrict__ x, const double* __restrict__ y,
@@ -169,12 +159,13 @@ __global__ void k_bbox_final(const double* __restrict__ part, int nblk, Cube* cu
 {
     part += (size_t)blockIdx.x * nblk * 6;  // cloud blockIdx.x
     Cube* cube = cubes + blockIdx.x;
-    __shared__ double s[256][6];
-    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    // min and max taken on the ordered integer images, as in k_bbox_partial
+    __shared__ unsigned long long s[256][6];
+    unsigned long long lo[3] = {~0ull, ~0ull, ~0ull}, hi[3] = {0ull, 0ull, 0ull};
     for (int b = threadIdx.x; b < nblk; b += blockDim.x)
         for (int a = 0; a < 3; ++a) {
-            lo[a] = fmin(lo[a], part[6 * b + a]);
-            hi[a] = fmax(hi[a], part[6 * b + 3 + a]);
+            lo[a] = min(lo[a], ord64(part[6 * b + a]));
+            hi[a] = max(hi[a], ord64(part[6 * b + 3 + a]));
         }
     for (int a = 0; a < 3; ++a) {
         s[threadIdx.x][a] = lo[a];
@@ -184,16 +175,17 @@ __global__ void k_bbox_final(const double* __restrict__ part, int nblk, Cube* cu
     for (int st = 128; st > 0; st >>= 1) {
         if ((int)threadIdx.x < st)
             for (int a = 0; a < 3; ++a) {
-                s[threadIdx.x][a] = fmin(s[threadIdx.x][a], s[threadIdx.x + st][a]);
-                s[threadIdx.x][3 + a] = fmax(s[threadIdx.x][3 + a], s[threadIdx.x + st][3 + a]);
+                s[threadIdx.x][a] = min(s[threadIdx.x][a], s[threadIdx.x + st][a]);
+                s[threadIdx.x][3 + a] = max(s[threadIdx.x][3 + a], s[threadIdx.x + st][3 + a]);
             }
         __syncthreads();
     }
     if (threadIdx.x != 0) return;
     double ext = 0.0;
     for (int a = 0; a < 3; ++a) {
-        cube->c[a] = __dmul_rn(__dadd_rn(s[0][a], s[0][3 + a]), 0.5);
-        double e = __dsub_rn(s[0][3 + a], s[0][a]);
+        const double mn = unord64(s[0][a]), mx = unord64(s[0][3 + a]);
+        cube->c[a] = __dmul_rn(__dadd_rn(mn, mx), 0.5);
+        double e = __dsub_rn(mx, mn);
         if (e > ext) ext = e;
     }
     double L = ext > 0.0 ? __dmul_rn(ext, 1.0 + 0x1p-20) : 1.0;

@@ -12,6 +12,19 @@ namespace ucp {
 constexpr int kMaxDepth = 21;        // 21 bits per axis, 63-bit keys
 constexpr int kWarp = 32;
 
+// Order-preserving integer image of a double (larger double, larger image; -0 below
+// +0; a NaN with the sign bit clear above every number, with it set below), so
+// min/max reductions are exact, order-independent integer operations.
+__device__ __forceinline__ unsigned long long ord64(double v)
+{
+    unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+__device__ __forceinline__ double unord64(unsigned long long u)
+{
+    return __longlong_as_double((long long)((u >> 63) ? (u & 0x7fffffffffffffffull) : ~u));
+}
+
 // Kernels launched by this process (read by ucp_stats).
 extern std::atomic<unsigned long long> g_launches;
 inline void count_launch(int k) { g_launches.fetch_add((unsigned long long)k, std::memory_order_relaxed); }

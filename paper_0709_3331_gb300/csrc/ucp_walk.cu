@@ -433,15 +433,29 @@ k_walk_fp32c(WalkArgs a)
                 const float4* P0;
                 if (st_cur) {
                     const int b = e & 1;
+                    const unsigned int par = (stage_phase >> b) & 1u;
                     bool done = false;
                     for (int it = 0; it < kStageSpin && !done; ++it)
-                        done = mbar_test(&stage_bar[w][b], (stage_phase >> b) & 1u);
+                        done = mbar_test(&stage_bar[w][b], par);
                     stage_phase ^= 1u << b;
                     P0 = &stage[w][b][0];
                     if (!done) {
                         // raise the flag, stop staging in this warp and read this
-                        // entry from global memory
+                        // entry from global memory; the copies still in flight into
+                        // this warp's buffers (this entry's, and the next entry's if
+                        // it was issued) get one more bounded wait each, so that none
+                        // lands after the warp has moved on
                         if (lane == 0) atomicExch(a.err, 1);
+                        bool late = false;
+                        for (int it = 0; it < kStageSpin && !late; ++it)
+                            late = mbar_test(&stage_bar[w][b], par);
+                        if (st_next) {
+                            const int b1 = b ^ 1;
+                            const unsigned int par1 = (stage_phase >> b1) & 1u;
+                            late = false;
+                            for (int it = 0; it < kStageSpin && !late; ++it)
+                                late = mbar_test(&stage_bar[w][b1], par1);
+                        }
                         stage_ok = false;
                         st_next = false;
                         P0 = S + ((size_t)__ldg(&a.t.info[nd].x) & ~(size_t)1);

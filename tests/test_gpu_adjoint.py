@@ -171,3 +171,80 @@ def test_tree_accel_autograd(U):
         p0 = torch.from_numpy(c.pos).to(dev).requires_grad_(True)
         assert torch.autograd.gradcheck(lambda x: tree_accel(x, sp, ctx, 0.0, 0.05), (p0,),
                                         eps=1e-6, atol=1e-6, rtol=1e-4)
+
+
+def _c4():
+    from paper_0709_3331_gb300.inputs import workload
+    c = workload("adjoint_n262144")
+    assert c.n == 262144
+    return c
+
+
+def test_gradient_fullsize_checkpoints(U):
+    """The differentiation workload at its own size (N = 262,144, sigma 6, theta
+    0.5, eps 0.01, leaf_cap 16, FP32C forces with FP64 state, dt_e 1e-3, k = 10):
+    over 40 electron substeps, a checkpoint every 20 substeps (forward
+    recomputation of each segment) gives the gradient of one unsegmented pass, up
+    to the rounding of the adjoint walk's atomic sums."""
+    c = _c4()
+    theta, eps, lc, dt, k, steps = 0.5, 0.01, 16, 1e-3, 10, 40
+    with U.Context(c.n, c.q, c.m, leaf_cap=lc, precision=1) as ctx:
+        ctx.set_state(c.pos, c.vel, c.species)
+        L, gx, gv = ctx.grad_ke_electrons(dt, k, steps, theta, eps, 20)
+        ctx.set_state(c.pos, c.vel, c.species)
+        L1, gx1, gv1 = ctx.grad_ke_electrons(dt, k, steps, theta, eps, steps)
+    assert L1 == L
+    assert rel_rms(gx, gx1) <= 1e-5 and rel_rms(gv, gv1) <= 1e-5
+
+
+def test_gradient_fullsize_finite_differences(U):
+    """The FP32C gradient at N = 262,144 (20 electron substeps, checkpoints every
+    10) against central differences, h = 1e-4, of the forward run on 64 seeded
+    coordinates (32 positions, 32 velocities).  The differences are taken on the
+    FP64 forward run: the FP32C run's rounding makes L (about 4e5) noisy at the
+    1e-4 level, which h = 1e-4 turns into O(1) noise in the quotient; the FP64
+    run's is ~1e-10.  A step of 1e-4 may cross an opening decision or a box
+    boundary, where the tree jumps (the adjoint holds the tree fixed); such
+    coordinates are counted, and most coordinates must agree to 1e-3."""
+    import torch
+    c = _c4()
+    theta, eps, lc, dt, k, steps, h = 0.5, 0.01, 16, 1e-3, 10, 20, 1e-4
+    dev = torch.device("cuda")
+    with U.Context(c.n, c.q, c.m, leaf_cap=lc, precision=1) as ctx:
+        ctx.set_state(c.pos, c.vel, c.species)
+        L, gx, gv = ctx.grad_ke_electrons(dt, k, steps, theta, eps, 10)
+    e = c.species == 1
+    sp_d = torch.from_numpy(c.species).to(dev)
+    with U.Context(c.n, c.q, c.m, leaf_cap=lc, precision=0) as ctx:
+
+        def loss(p, v):
+            ctx.set_state(torch.from_numpy(p).to(dev), torch.from_numpy(v).to(dev), sp_d)
+            ctx.step(dt, k, steps, theta, eps)
+            _, vv = ctx.get_state()
+            return 0.5 * c.m[1] * (vv[e] ** 2).sum()
+
+        # the FP64 run ends within the FP32C force rounding of the FP32C run
+        assert loss(c.pos, c.vel) == pytest.approx(L, rel=1e-6)
+        rng = np.random.default_rng(11)
+        idx = rng.choice(c.n, 32, replace=False)
+        res = {"x": [], "v": []}
+        for which, g in (("x", gx), ("v", gv)):
+            floor = 2e-4 * math.sqrt((g ** 2).mean())
+            for i in idx:
+                a = int(rng.integers(3))
+                p, v = c.pos.copy(), c.vel.copy()
+                arr = p if which == "x" else v
+                arr[i, a] += h
+                lp = loss(p, v)
+                arr[i, a] -= 2 * h
+                lm = loss(p, v)
+                fd = (lp - lm) / (2 * h)
+                err = abs(fd - g[i, a])
+                res[which].append((err <= 1e-3 * abs(fd) + floor, err / max(abs(fd), 1e-30)))
+    rel = np.array([r for w in res for _, r in res[w]])
+    good = {w: sum(ok for ok, _ in res[w]) for w in res}
+    assert rel.size == 64
+    # the bulk agrees far inside the bar; decision jumps are a minority
+    assert np.median(rel) <= 1e-4, np.median(rel)
+    print("c4 finite differences: agree", good, "median rel", np.median(rel), "worst", np.sort(rel)[-6:])
+    assert good["v"] >= 30 and good["x"] >= 24, (good, np.sort(rel)[-10:])

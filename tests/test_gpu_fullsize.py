@@ -2,8 +2,8 @@
 k = 10), the precision workload the benchmark times, in the walk launch shape
 the autotuner picks for it.  The oracle computes sampled targets one by one on
 the GPU's own state, at electron steps 0, 50 and 100 of the split-step run, and
-the opening angles 0.3, 0.5 and 0.7 at step 0; the direct sum on a smaller
-sample checks that the GPU's tree error is the oracle's tree error."""
+the opening angles 0.3, 0.5 and 0.7 at step 0; the direct sum on 8192
+sampled targets checks that the GPU's tree error is the oracle's tree error."""
 import math
 import os
 
@@ -52,9 +52,23 @@ def _oracle(orc, pos, c, theta, tl):
     return E * qm, phi, npp, nmp
 
 
+def _direct(orc, pos, c, tl):
+    E, _ = orc.direct(pos, c.species, c.q, 0.01, targets=tl, nthreads=NTHREADS)
+    return E * (c.q[c.species[tl]] / c.m[c.species[tl]])[:, None]
+
+
+def _per_target_rel(a, b):
+    return np.linalg.norm(a - b, axis=1) / np.linalg.norm(b, axis=1)
+
+
 def test_fullsize_fp32c_steps_0_50_100(U, orc, cloud):
+    """At electron steps 0, 50 and 100: the GPU tree against the oracle tree
+    (<= 1e-4) on 8192 seeded targets, and both against the direct sum on the same
+    targets (the method's own error, Eq. 5): the GPU's error is the oracle's.
+    Targets whose FP32C opening decisions differ from the oracle's (at most 0.1 %)
+    keep a force within the tree's own per-target error against the direct sum."""
     c = cloud
-    tl = _sample(c.n, 4096, 50)
+    tl = _sample(c.n, 8192, 50)
     with U.Context(c.n, c.q, c.m, leaf_cap=16, precision=U.UCP_FP32C) as ctx:
         ctx.set_state(c.pos, c.vel, c.species)
         ctx.autotune(0.5, 0.01)
@@ -68,8 +82,17 @@ def test_fullsize_fp32c_steps_0_50_100(U, orc, cloud):
             a_ref, p_ref, npp, nmp = _oracle(orc, pos, c, 0.5, tl)
             assert rel_rms(acc[tl], a_ref) <= FP32C_TOL, step
             assert rel_rms(phi[tl], p_ref) <= FP32C_TOL, step
-            mism = np.count_nonzero((gp[tl] != npp) | (gm[tl] != nmp))
-            assert mism <= 2 + tl.size // 1000, (step, mism)
+            a_dir = _direct(orc, pos, c, tl)
+            err_gpu, err_orc = rel_rms(acc[tl], a_dir), rel_rms(a_ref, a_dir)
+            assert err_orc < 1e-2, (step, err_orc)
+            assert abs(err_gpu - err_orc) <= FP32C_TOL, (step, err_gpu, err_orc)
+            flip = (gp[tl] != npp) | (gm[tl] != nmp)
+            assert np.count_nonzero(flip) <= 2 + tl.size // 1000, (step, np.count_nonzero(flip))
+            if flip.any():
+                tree_err = _per_target_rel(a_ref, a_dir)
+                bound = np.quantile(tree_err, 0.99)
+                got = _per_target_rel(acc[tl][flip], a_dir[flip])
+                assert (got <= np.maximum(bound, 2 * tree_err[flip])).all(), (step, got, bound)
 
 
 @pytest.mark.parametrize("prec,theta", [(0, 0.3), (0, 0.5), (0, 0.7), (1, 0.3), (1, 0.7)])
@@ -90,18 +113,19 @@ def test_fullsize_theta(U, orc, cloud, prec, theta):
     assert mism <= 2 + tl.size // 1000, mism
 
 
-def test_fullsize_tree_error_vs_direct(U, orc, cloud):
+@pytest.mark.parametrize("theta", [0.3, 0.7])
+def test_fullsize_tree_error_vs_direct(U, orc, cloud, theta):
+    """The method's error at the other opening angles (step 0, 8192 targets): the
+    GPU's error against the direct sum is the oracle tree's, to FP32 rounding."""
     c = cloud
-    tl = _sample(c.n, 512, 99)
+    tl = _sample(c.n, 8192, 99)
     with U.Context(c.n, c.q, c.m, leaf_cap=16, precision=U.UCP_FP32C) as ctx:
         ctx.set_state(c.pos, c.vel, c.species)
-        acc, _ = ctx.tree_force(0.5, 0.01)
-    E, _ = orc.direct(c.pos, c.species, c.q, 0.01, targets=tl, nthreads=NTHREADS)
-    a_dir = E * (c.q[c.species[tl]] / c.m[c.species[tl]])[:, None]
-    a_tree, _, _, _ = _oracle(orc, c.pos, c, 0.5, tl)
+        acc, _ = ctx.tree_force(theta, 0.01)
+    a_dir = _direct(orc, c.pos, c, tl)
+    a_tree, _, _, _ = _oracle(orc, c.pos, c, theta, tl)
     err_gpu = rel_rms(acc[tl], a_dir)
     err_orc = rel_rms(a_tree, a_dir)
-    # the expansion error at theta 0.5 is well below a percent, and the GPU's
-    # error differs from the oracle's only by its FP32 rounding
-    assert err_orc < 1e-2
+    # the expansion error stays below a few percent and shrinks with theta
+    assert err_orc < (1e-2 if theta <= 0.5 else 3e-2)
     assert abs(err_gpu - err_orc) <= FP32C_TOL

@@ -150,11 +150,24 @@ def test_force_fp32c(U, orc, n, sigma, seed, leaf_cap, theta):
         gp, gm = ctx.get_counts()
     assert rel_rms(acc, a_ref) <= FP32C_TOL
     assert rel_rms(ph, phi) <= FP32C_TOL
-    # borderline FP32 decisions are retaken in FP64; the FP32 pseudo-particle
-    # positions differ from the oracle's by ~1e-7 of a box side, so a decision that
-    # close to the threshold may go either way: at most 0.1 % of targets differ
-    mism = np.count_nonzero((gp != npp) | (gm != nmp))
-    assert mism <= 2 + n // 1000, mism
+    # borderline FP32 decisions are retaken in FP64; the FP32C moments (and so the
+    # pseudo-particle positions) differ from the oracle's by ~1e-7 of a box side, so
+    # a decision that close to the threshold may go either way: at most 0.1 % of
+    # targets differ, and each such target's field stays within the tree's own
+    # per-target error against the direct sum
+    flip = (gp != npp) | (gm != nmp)
+    assert np.count_nonzero(flip) <= 2 + n // 1000, np.count_nonzero(flip)
+    if flip.any():
+        tl = np.nonzero(flip)[0]
+        Ed, _ = orc.direct(c.pos, c.species, c.q, eps, targets=tl, nthreads=4)
+        a_dir = Ed * (c.q[c.species[tl]] / c.m[c.species[tl]])[:, None]
+        samp = np.random.default_rng(0).choice(n, min(n, 256), replace=False)
+        Es, _ = orc.direct(c.pos, c.species, c.q, eps, targets=samp, nthreads=4)
+        a_s = Es * (c.q[c.species[samp]] / c.m[c.species[samp]])[:, None]
+        tree_err = np.linalg.norm(a_ref[samp] - a_s, axis=1) / np.linalg.norm(a_s, axis=1)
+        own = np.linalg.norm(a_ref[tl] - a_dir, axis=1) / np.linalg.norm(a_dir, axis=1)
+        got = np.linalg.norm(acc[tl] - a_dir, axis=1) / np.linalg.norm(a_dir, axis=1)
+        assert (got <= np.maximum(np.quantile(tree_err, 0.99), 2 * own)).all(), got
 
 
 def test_force_edge_cases(U, orc):
