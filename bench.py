@@ -155,9 +155,28 @@ def oracle_sample(cloud, n_targets, nthreads, seed=0):
     return dt, int(npp.sum() + nmp.sum())
 
 
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo), for the record."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part")):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return None
+
+
 def cpu_baseline(cloud, budget_s=12.0):
     """The oracle as it stands on the host cores: tree build + walk of every
-    particle, repeated until about budget_s seconds of CPU work."""
+    particle, repeated until about budget_s seconds of CPU work; and the same
+    oracle on one core (tree build + walk of a seeded eighth of the targets)."""
     from oracle import oracle as O
     O.build()
     cores = os.cpu_count() or 1
@@ -171,10 +190,55 @@ def cpu_baseline(cloud, budget_s=12.0):
         reps += 1
         if reps == 1 and dt > budget_s:
             break
+    t1, i1 = oracle_sample(cloud, cloud.n // 8, 1, seed=77)
     return {"value": tot_i / tot_t, "unit": UNIT, "cores": nthreads, "kind": "oracle",
+            "cpu_model": cpu_model(), "host_cores": cores,
             "sample": f"FP64 serial-tree oracle, {reps} x (tree build over all {cloud.n} "
                       f"particles + walk of all {nt} targets, theta {WORKLOAD['theta']}, "
-                      f"leaf_cap {WORKLOAD['leaf_cap']}), OpenMP over targets, {tot_t:.1f} s"}
+                      f"leaf_cap {WORKLOAD['leaf_cap']}), OpenMP over targets, {tot_t:.1f} s",
+            "one_core": {"value": i1 / t1, "unit": UNIT, "cores": 1,
+                         "sample": f"tree build over all {cloud.n} particles + walk of "
+                                   f"{cloud.n // 8} seeded targets on one thread, {t1:.1f} s"}}
+
+
+def oracle_accuracy(cloud, tl, gpu, nthreads):
+    """Force and potential errors on the seeded targets tl: the GPU tree (given,
+    per theta) and the oracle tree against the direct sum (Sec. 2.1 Eq. 1-2), and
+    the GPU tree against the oracle tree, all at the workload's initial state."""
+    from oracle import oracle as O
+    c = cloud
+    qm = (c.q[c.species[tl]] / c.m[c.species[tl]])[:, None]
+    Ed, pd = O.direct(c.pos, c.species, c.q, WORKLOAD["eps"], targets=tl, nthreads=nthreads)
+    ad = Ed * qm
+    T = O.Tree(c.pos, c.species, c.q, leaf_cap=WORKLOAD["leaf_cap"])
+
+    def rr(a, b):
+        return float(np.sqrt(((a - b) ** 2).sum() / (b ** 2).sum()))
+
+    out = {}
+    for th, (ga, gp) in gpu.items():
+        Et, pt = T.force(float(th), WORKLOAD["eps"], targets=tl, nthreads=nthreads)
+        at = Et * qm
+        out[th] = {"gpu_tree_vs_direct": {"force": rr(ga, ad), "potential": rr(gp, pd)},
+                   "oracle_tree_vs_direct": {"force": rr(at, ad), "potential": rr(pt, pd)},
+                   "gpu_vs_oracle_tree": {"force": rr(ga, at), "potential": rr(gp, pt)}}
+    return out
+
+
+def oracle_drift_c1(steps, nthreads):
+    """Total-energy drift of the oracle at the plain FP64 workload (N = 131072,
+    sigma 4, theta 0.5, eps 0.01, dt_e 1e-3, k = 10) over a short span."""
+    from oracle import oracle as O
+    from paper_0709_3331_gb300.inputs import gaussian_cloud
+    c1 = gaussian_cloud(131072, 4.0, 2)
+    lc, th, eps, dt, k = WORKLOAD["leaf_cap"], 0.5, WORKLOAD["eps"], 1e-3, 10
+    e0 = O.energy(c1.pos, c1.vel, c1.species, c1.q, c1.m, th, eps, leaf_cap=lc, nthreads=nthreads)
+    t0 = time.perf_counter()
+    p, v, _ = O.run(c1.pos, c1.vel, c1.species, c1.q, c1.m, dt, k, steps // k, th, eps,
+                    leaf_cap=lc, nthreads=nthreads)
+    t = time.perf_counter() - t0
+    e1 = O.energy(p, v, c1.species, c1.q, c1.m, th, eps, leaf_cap=lc, nthreads=nthreads)
+    return abs(e1[3] - e0[3]) / (e0[0] + e0[1] + abs(e0[2])), t
 
 
 def run_reference(args):
@@ -339,6 +403,15 @@ def run_gpu(args):
                 "walk_ms_per_launch": walk_ms / max(walk_n, 1), "walk_launches": walk_n,
                 "walk_share_of_step": walk_ms / ms if ms > 0 else None}
 
+    # forces of the initial state on seeded targets, for the accuracy figures
+    ACC_TARGETS = 8192
+    tl = np.sort(np.random.default_rng(2024).choice(W["n"], ACC_TARGETS, replace=False))
+    acc_d = torch.empty((W["n"], 3), dtype=torch.float64, device=dev)
+    phi_d = torch.empty(W["n"], dtype=torch.float64, device=dev)
+    ctx.set_state(pos_d, vel_d, sp_d)
+    ctx.tree_force(W["theta"], W["eps"], acc_d, phi_d)
+    gpu_samples = {str(W["theta"]): (acc_d.cpu().numpy()[tl], phi_d.cpu().numpy()[tl])}
+
     # ---------------- e2e through the public API with host buffers
     e2e = None
     if not args.no_e2e:
@@ -348,7 +421,7 @@ def run_gpu(args):
     extra = {}
     if not args.quick:
         extra = run_extras(c, W, ws, pos_d, vel_d, sp_d, Context, UCP_FP32C, UCP_FP64,
-                           timed_steps, flush, stream, peak, ms / args.steps)
+                           timed_steps, flush, stream, peak, ms / args.steps, tl, gpu_samples)
 
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -381,7 +454,31 @@ def run_gpu(args):
     out.update(extra)
     ctx.close()
     if rank == 0 and not args.no_cpu_baseline:
+        # the oracle leg: host-core timings, the direct-sum accuracy reference and
+        # the oracle's own drift at the plain workload
         out["cpu_baseline"] = cpu_baseline(c)
+        from oracle import oracle as O
+        nthr = (os.cpu_count() or 1) if O.has_openmp() else 1
+        accs = oracle_accuracy(c, tl, gpu_samples, nthr)
+        a0 = accs[str(W["theta"])]
+        out["accuracy"] = {
+            "force_rel_rms_vs_direct": a0["gpu_tree_vs_direct"]["force"],
+            "potential_rel_rms_vs_direct": a0["gpu_tree_vs_direct"]["potential"],
+            "oracle_tree_force_rel_rms_vs_direct": a0["oracle_tree_vs_direct"]["force"],
+            "force_rel_rms_vs_oracle_tree": a0["gpu_vs_oracle_tree"]["force"],
+            "theta": W["theta"], "leaf_cap": W["leaf_cap"], "targets": int(tl.size),
+            "state": "initial state of the workload; FP32C tree forces against the FP64 direct "
+                     "sum on seeded targets (oracle)"}
+        for th, a in accs.items():
+            if "theta_sweep" in out and th in out["theta_sweep"]:
+                out["theta_sweep"][th]["accuracy"] = a
+        if "plain_fp64_n131072" in out:
+            d_orc, t_orc = oracle_drift_c1(10, nthr)
+            out["plain_fp64_n131072"]["drift_10_substeps"] = {
+                "gpu": out["plain_fp64_n131072"].pop("drift_10_substeps_gpu"), "oracle": d_orc,
+                "oracle_s": t_orc,
+                "note": "one block of 10 electron substeps from the same state, GPU FP64 walk "
+                        "vs the FP64 CPU oracle"}
     if rank == 0:
         print(json.dumps(out))
     if ws > 1:
@@ -437,7 +534,7 @@ def run_e2e(c, W, args, ws, dev, flush, Context, UCP_FP32C):
 
 
 def run_extras(c, W, ws, pos_d, vel_d, sp_d, Context, UCP_FP32C, UCP_FP64, timed_steps, flush,
-               stream, peak, ms_step32):
+               stream, peak, ms_step32, tl, gpu_samples):
     import torch
     extra = {}
     ctx64 = Context(c.n, c.q, c.m, leaf_cap=W["leaf_cap"], precision=UCP_FP64)
@@ -455,6 +552,11 @@ def run_extras(c, W, ws, pos_d, vel_d, sp_d, Context, UCP_FP32C, UCP_FP64, timed
     for th in (0.3, 0.5, 0.7):
         cs = Context(c.n, c.q, c.m, leaf_cap=W["leaf_cap"], precision=UCP_FP32C)
         cs.set_state(pos_d, vel_d, sp_d)
+        if str(th) not in gpu_samples:
+            a_s, p_s = cs.tree_force(th, W["eps"], torch.empty((c.n, 3), dtype=torch.float64,
+                                                              device=pos_d.device),
+                                     torch.empty(c.n, dtype=torch.float64, device=pos_d.device))
+            gpu_samples[str(th)] = (a_s.cpu().numpy()[tl], p_s.cpu().numpy()[tl])
         cs.set_graphs(True)
         cs.profile(True)
         cs.step(W["dt_e"], W["k"], W["k"], th, W["eps"])
@@ -552,6 +654,12 @@ def run_extras(c, W, ws, pos_d, vel_d, sp_d, Context, UCP_FP32C, UCP_FP64, timed
     cp = Context(c1.n, c1.q, c1.m, leaf_cap=W["leaf_cap"], precision=UCP_FP64)
     cp.set_state(c1.pos, c1.vel, c1.species)
     e0 = cp.energy(0.5, W["eps"])
+    # one block from the same state (compared with the oracle's block in the oracle leg)
+    cp.step(W["dt_e"], W["k"], W["k"], 0.5, W["eps"])
+    e10 = cp.energy(0.5, W["eps"])
+    drift10 = abs(e10[3] - e0[3]) / (e0[0] + e0[1] + abs(e0[2]))
+    cp.set_state(c1.pos, c1.vel, c1.species)
+    e0 = cp.energy(0.5, W["eps"])
     torch.cuda.synchronize()
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
@@ -622,8 +730,26 @@ def run_extras(c, W, ws, pos_d, vel_d, sp_d, Context, UCP_FP32C, UCP_FP64, timed
 
     extra["plain_fp64_n131072"] = {
         "electron_steps": 1000, "ms": mp, "particle_steps_per_s": c1.n * 1000 / (mp / 1e3),
-        "energy_drift": abs(e1[3] - e0[3]) / (e0[0] + e0[1] + abs(e0[2]))}
+        "energy_drift": abs(e1[3] - e0[3]) / (e0[0] + e0[1] + abs(e0[2])),
+        "drift_10_substeps_gpu": drift10}
     cp.close()
+    # the same workload: drift over t = 0.5 against the electron step (FP32C walk,
+    # captured blocks); close e-i encounters are resolved as dt_e falls
+    dv = {}
+    for dt in (1e-3, 5e-4, 2.5e-4, 1.25e-4):
+        cd = Context(c1.n, c1.q, c1.m, leaf_cap=W["leaf_cap"], precision=UCP_FP32C)
+        cd.set_state(c1.pos, c1.vel, c1.species)
+        cd.set_graphs(True)
+        d0 = cd.energy(0.5, W["eps"])
+        nsub = int(round(0.5 / dt))
+        cd.step(dt, W["k"], nsub, 0.5, W["eps"])
+        d1 = cd.energy(0.5, W["eps"])
+        dv[f"{dt:g}"] = {"substeps": nsub,
+                         "energy_drift": abs(d1[3] - d0[3]) / (d0[0] + d0[1] + abs(d0[2]))}
+        cd.close()
+    extra["plain_n131072_drift_vs_dt"] = {
+        "t": 0.5, "by_dt_e": dv,
+        "note": "FP32C walk (forces within 1e-6 of FP64); drift = |E(t) - E(0)| / (KE + |PE|)"}
     return extra
 
 
