@@ -626,6 +626,72 @@ __global__ void k_clear_children(Tree t)
         t.child8[i] = -1;
 }
 
+// Moments of twig p (depth d) from its eight child slots in octant order, each
+// child's moments shifted to the twig's geometric centre.  The children were
+// written by other threads of the same launch: their records are read through
+// L2 (__ldcg) after the fence of the bottom-up sweep.
+__device__ void twig_combine_f64(const Cube* __restrict__ cube, const Tree& t, int p, int d)
+{
+    const Cube cb = cube_of(cube, t, t.info[p].x);
+    double zp[3], ps;
+    box_centre(cb, t.cell[p], d, zp, &ps);
+    double a[14];
+#pragma unroll
+    for (int k = 0; k < 14; ++k) a[k] = 0.0;
+#pragma unroll 1
+    for (int o = 0; o < 8; ++o) {
+        const int ch = t.child8[(size_t)p * 8 + o];
+        if (ch < 0) continue;
+        const double* cm = t.mom + (size_t)ch * kMom;
+        double S0k = __ldcg(cm + MS0), Mk = __ldcg(cm + MM);
+        double e[3], dk[3], qk[6];
+        for (int k = 0; k < 3; ++k) {
+            e[k] = __ldcg(cm + MC + k) - zp[k];
+            dk[k] = __ldcg(cm + MD + k);
+        }
+        for (int k = 0; k < 6; ++k) qk[k] = __ldcg(cm + MQ + k);
+        a[0] += S0k;
+        a[1] += Mk;
+        for (int k = 0; k < 3; ++k) {
+            a[2 + k] += S0k * e[k];
+            a[5 + k] += dk[k] + Mk * e[k];
+        }
+        // Q_k + D_k e^T + e D_k^T + M_k e e^T
+        double me0 = Mk * e[0], me1 = Mk * e[1], me2 = Mk * e[2];
+        a[8] += qk[0] + (2.0 * dk[0] + me0) * e[0];
+        a[9] += qk[1] + dk[0] * e[1] + (dk[1] + me1) * e[0];
+        a[10] += qk[2] + dk[0] * e[2] + (dk[2] + me2) * e[0];
+        a[11] += qk[3] + (2.0 * dk[1] + me1) * e[1];
+        a[12] += qk[4] + dk[1] * e[2] + (dk[2] + me2) * e[1];
+        a[13] += qk[5] + (2.0 * dk[2] + me2) * e[2];
+    }
+    double rec[kMom];
+    finish_box(a, zp, rec);
+    double* pm = t.mom + (size_t)p * kMom;
+#pragma unroll
+    for (int k = 0; k < kMom; ++k) pm[k] = rec[k];
+}
+
+// Bottom-up sweep from a finished box: each box counts its finished children
+// (t.arrive, zeroed before the launch); the thread that finishes the last child
+// combines the parent and carries on upwards.  No thread waits for another, and
+// every twig is combined once, from all its children, whichever thread does it.
+template <class Combine>
+__device__ __forceinline__ void sweep_up(const Tree& t, int node, Combine combine)
+{
+    int p = t.info[node].w;
+    while (p >= 0) {
+        int nch = 0;
+#pragma unroll
+        for (int o = 0; o < 8; ++o) nch += t.child8[(size_t)p * 8 + o] >= 0;
+        __threadfence();  // this box's records before its arrival is counted
+        if (atomicAdd(&t.arrive[p], 1) + 1 < nch) return;
+        __threadfence();  // the other children's records before they are read
+        combine(p, t.depth_leaf[p] & 255);
+        p = t.info[p].w;
+    }
+}
+
 // Moments of every leaf from its particles, one thread per leaf, summed about
 // the leaf's geometric centre in key order.
 __global__ void __launch_bounds__(256)
@@ -683,65 +749,7 @@ k_moments_leaves(const double* __restrict__ x, const double* __restrict__ y,
                 f[b + 6] = (float)qj;
             }
         }
-    }
-}
-
-// Moments of the twigs of one depth, one thread per twig: the eight child slots
-// in octant order, each child's moments shifted to the twig's geometric centre.
-// Depths are processed from the deepest up, one launch each, so every child is
-// complete; the arithmetic of a twig does not depend on the schedule.
-__global__ void __launch_bounds__(256)
-k_moments_twigs(const Cube* __restrict__ cube, Tree t, int d_hi, int d_lo)
-{
-    // several depths in one launch only with a single block (barrier between depths)
-    for (int d = d_hi; d >= d_lo; --d) {
-    const int nt = t.count[d];
-    const int* __restrict__ list = t.twig_list + t.twig_off[d];
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nt; i += gridDim.x * blockDim.x) {
-        const int p = list[i];
-        const Cube cb = cube_of(cube, t, t.info[p].x);
-        double zp[3], ps;
-        box_centre(cb, t.cell[p], d, zp, &ps);
-        const int4 c03 = *reinterpret_cast<const int4*>(t.child8 + (size_t)p * 8);
-        const int4 c47 = *reinterpret_cast<const int4*>(t.child8 + (size_t)p * 8 + 4);
-        const int chs[8] = {c03.x, c03.y, c03.z, c03.w, c47.x, c47.y, c47.z, c47.w};
-        double a[14];
-#pragma unroll
-        for (int k = 0; k < 14; ++k) a[k] = 0.0;
-#pragma unroll 1
-        for (int o = 0; o < 8; ++o) {
-            const int ch = chs[o];
-            if (ch < 0) continue;
-            const double* cm = t.mom + (size_t)ch * kMom;
-            double S0k = cm[MS0], Mk = cm[MM];
-            double e[3], dk[3], qk[6];
-            for (int k = 0; k < 3; ++k) {
-                e[k] = cm[MC + k] - zp[k];
-                dk[k] = cm[MD + k];
-            }
-            for (int k = 0; k < 6; ++k) qk[k] = cm[MQ + k];
-            a[0] += S0k;
-            a[1] += Mk;
-            for (int k = 0; k < 3; ++k) {
-                a[2 + k] += S0k * e[k];
-                a[5 + k] += dk[k] + Mk * e[k];
-            }
-            // Q_k + D_k e^T + e D_k^T + M_k e e^T
-            double me0 = Mk * e[0], me1 = Mk * e[1], me2 = Mk * e[2];
-            a[8] += qk[0] + (2.0 * dk[0] + me0) * e[0];
-            a[9] += qk[1] + dk[0] * e[1] + (dk[1] + me1) * e[0];
-            a[10] += qk[2] + dk[0] * e[2] + (dk[2] + me2) * e[0];
-            a[11] += qk[3] + (2.0 * dk[1] + me1) * e[1];
-            a[12] += qk[4] + dk[1] * e[2] + (dk[2] + me2) * e[1];
-            a[13] += qk[5] + (2.0 * dk[2] + me2) * e[2];
-        }
-        double rec[kMom];
-        finish_box(a, zp, rec);
-        double* pm = t.mom + (size_t)p * kMom;
-#pragma unroll
-        for (int k = 0; k < kMom; ++k) pm[k] = rec[k];
-    }
-    if (d > d_lo) __syncthreads();
+        sweep_up(t, node, [&](int p, int d) { twig_combine_f64(cube, t, p, d); });
     }
 }
 
@@ -780,17 +788,73 @@ __device__ __forceinline__ void finish_box_f32(const float* a, const double z[3]
     m64[MDELTA] = sqrtf(fmaf(e[0], e[0], fmaf(e[1], e[1], e[2] * e[2])));
 }
 
-// Sum of v over the aligned group of G lanes that holds this lane (xor butterfly,
-// the same order in every group).
-template <int G>
-__device__ __forceinline__ float group_sum(float v)
+// Child slot o of twig p shifted to the twig's centre zp (zeros for an empty slot).
+__device__ __forceinline__ void twig_child_f32(const Tree& t, int p, int o, const double zp[3],
+                                               float* a)
 {
 #pragma unroll
-    for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
+    for (int k = 0; k < 14; ++k) a[k] = 0.f;
+    const int ch = t.child8[(size_t)p * 8 + o];
+    if (ch < 0) return;
+    const double* cm = t.mom + (size_t)ch * kMom;
+    const float4* r32 = reinterpret_cast<const float4*>(t.mom32 + (size_t)ch * 16);
+    const float4 R0 = __ldcg(r32), R1 = __ldcg(r32 + 1), R2 = __ldcg(r32 + 2),
+                 R3 = __ldcg(r32 + 3);
+    const float S0k = R0.w, Mk = R1.x;
+    const float dk[3] = {R1.y, R1.z, R1.w};
+    const float qk[6] = {R2.x, R2.y, R2.z, R2.w, R3.x, R3.y};
+    float e[3];
+    for (int k = 0; k < 3; ++k) e[k] = (float)(__ldcg(cm + MC + k) - zp[k]);
+    a[0] = S0k;
+    a[1] = Mk;
+    for (int k = 0; k < 3; ++k) {
+        a[2 + k] = S0k * e[k];
+        a[5 + k] = fmaf(Mk, e[k], dk[k]);
+    }
+    float me0 = Mk * e[0], me1 = Mk * e[1], me2 = Mk * e[2];
+    a[8] = qk[0] + (2.f * dk[0] + me0) * e[0];
+    a[9] = qk[1] + dk[0] * e[1] + (dk[1] + me1) * e[0];
+    a[10] = qk[2] + dk[0] * e[2] + (dk[2] + me2) * e[0];
+    a[11] = qk[3] + (2.f * dk[1] + me1) * e[1];
+    a[12] = qk[4] + dk[1] * e[2] + (dk[2] + me2) * e[1];
+    a[13] = qk[5] + (2.f * dk[2] + me2) * e[2];
 }
 
-// Leaves, one thread per leaf (full lanes for the FP64 offsets).
+// FP32 moments of twig p (depth d) from its eight shifted child slots, summed as
+// ((s0 + s4) + (s2 + s6)) + ((s1 + s5) + (s3 + s7)): the order of an xor
+// butterfly over the slots.
+__device__ void twig_combine_f32(const Cube* __restrict__ cube, const Tree& t, int p, int d)
+{
+    const Cube cb = cube_of(cube, t, t.info[p].x);
+    double zp[3], ps;
+    box_centre(cb, t.cell[p], d, zp, &ps);
+    float u[14], v[14], w[14];
+    const int order[4][2] = {{0, 4}, {2, 6}, {1, 5}, {3, 7}};
+#pragma unroll 1
+    for (int g = 0; g < 4; ++g) {
+        float b0[14], b1[14];
+        twig_child_f32(t, p, order[g][0], zp, b0);
+        twig_child_f32(t, p, order[g][1], zp, b1);
+#pragma unroll
+        for (int k = 0; k < 14; ++k) {
+            const float s = b0[k] + b1[k];
+            if (g == 0) u[k] = s;
+            else if (g == 1) u[k] = u[k] + s;
+            else if (g == 2) v[k] = s;
+            else v[k] = v[k] + s;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 14; ++k) w[k] = u[k] + v[k];
+    float m32[16];
+    finish_box_f32(w, zp, m32, t.mom + (size_t)p * kMom);
+    float4* w32 = reinterpret_cast<float4*>(t.mom32 + (size_t)p * 16);
+    for (int k = 0; k < 4; ++k)
+        w32[k] = make_float4(m32[4 * k], m32[4 * k + 1], m32[4 * k + 2], m32[4 * k + 3]);
+}
+
+// Leaves, one thread per leaf (full lanes for the FP64 offsets), then the
+// bottom-up sweep over the twigs (sweep_up).
 __global__ void __launch_bounds__(256)
 k_moments_leaves_f32(const double* __restrict__ x, const double* __restrict__ y,
                      const double* __restrict__ z, const int8_t* __restrict__ sp,
@@ -846,68 +910,7 @@ k_moments_leaves_f32(const double* __restrict__ x, const double* __restrict__ y,
             f[b + 4] = (float)(cz - z[j]);
             f[b + 6] = sp[j] ? q1 : q0;
         }
-    }
-}
-
-// Twigs, 8 lanes per twig: lane o shifts child slot o to the twig's centre,
-// the group sums the eight contributions.
-__global__ void __launch_bounds__(256)
-k_moments_twigs_f32(const Cube* __restrict__ cube, Tree t, int d_hi, int d_lo)
-{
-    constexpr int G = 8;
-    const int o = threadIdx.x & (G - 1);
-    const int groups = gridDim.x * (blockDim.x / G);
-    const int first = blockIdx.x * (blockDim.x / G) + (threadIdx.x / G);
-    const int warp_first = first & ~3;
-    // several depths in one launch only with a single block (barrier between depths)
-    for (int d = d_hi; d >= d_lo; --d) {
-        const int nt = t.count[d];
-        const int* __restrict__ list = t.twig_list + t.twig_off[d];
-        for (int base = warp_first; base < nt; base += groups) {
-            const int i = base + (first & 3);
-            const bool have = i < nt;
-            const int p = have ? list[i] : 0;
-            const Cube cb = cube_of(cube, t, have ? t.info[p].x : 0);
-            double zp[3], ps;
-            box_centre(cb, have ? t.cell[p] : 0ull, d, zp, &ps);
-            const int ch = have ? t.child8[(size_t)p * 8 + o] : -1;
-            float a[14];
-#pragma unroll
-            for (int k = 0; k < 14; ++k) a[k] = 0.f;
-            if (ch >= 0) {
-                const double* cm = t.mom + (size_t)ch * kMom;
-                const float4* r32 = reinterpret_cast<const float4*>(t.mom32 + (size_t)ch * 16);
-                const float4 R0 = r32[0], R1 = r32[1], R2 = r32[2], R3 = r32[3];
-                const float S0k = R0.w, Mk = R1.x;
-                const float dk[3] = {R1.y, R1.z, R1.w};
-                const float qk[6] = {R2.x, R2.y, R2.z, R2.w, R3.x, R3.y};
-                float e[3];
-                for (int k = 0; k < 3; ++k) e[k] = (float)(cm[MC + k] - zp[k]);
-                a[0] = S0k;
-                a[1] = Mk;
-                for (int k = 0; k < 3; ++k) {
-                    a[2 + k] = S0k * e[k];
-                    a[5 + k] = fmaf(Mk, e[k], dk[k]);
-                }
-                float me0 = Mk * e[0], me1 = Mk * e[1], me2 = Mk * e[2];
-                a[8] = qk[0] + (2.f * dk[0] + me0) * e[0];
-                a[9] = qk[1] + dk[0] * e[1] + (dk[1] + me1) * e[0];
-                a[10] = qk[2] + dk[0] * e[2] + (dk[2] + me2) * e[0];
-                a[11] = qk[3] + (2.f * dk[1] + me1) * e[1];
-                a[12] = qk[4] + dk[1] * e[2] + (dk[2] + me2) * e[1];
-                a[13] = qk[5] + (2.f * dk[2] + me2) * e[2];
-            }
-#pragma unroll
-            for (int k = 0; k < 14; ++k) a[k] = group_sum<G>(a[k]);
-            if (have && o == 0) {
-                float m32[16];
-                finish_box_f32(a, zp, m32, t.mom + (size_t)p * kMom);
-                float4* w32 = reinterpret_cast<float4*>(t.mom32 + (size_t)p * 16);
-                for (int k = 0; k < 4; ++k)
-                    w32[k] = make_float4(m32[4 * k], m32[4 * k + 1], m32[4 * k + 2], m32[4 * k + 3]);
-            }
-        }
-        if (d > d_lo) __syncthreads();
+        sweep_up(t, node, [&](int p, int d) { twig_combine_f32(cube, t, p, d); });
     }
 }
 
@@ -1028,7 +1031,10 @@ void launch_moments(const double* x, const double* y, const double* z, const int
                     const double* qsp, int n, const Cube* cube, Tree t, float4* src32,
                     int want_f32, cudaStream_t s)
 {
-    count_launch(1 + 12);
+    // leaves from their particles, then every twig as its last child finishes
+    // (bottom-up sweep with arrival counters), in one launch
+    count_launch(1);
+    cudaMemsetAsync(t.arrive, 0, sizeof(int) * (size_t)t.cap, s);
     int blocks = (n + 255) / 256;
     if (blocks > 4 * 152) blocks = 4 * 152;
     if (blocks < 1) blocks = 1;
@@ -1036,20 +1042,6 @@ void launch_moments(const double* x, const double* y, const double* z, const int
         k_moments_leaves_f32<<<blocks, 256, 0, s>>>(x, y, z, sp, qsp, cube, t, src32);
     else
         k_moments_leaves<<<blocks, 256, 0, s>>>(x, y, z, sp, qsp, cube, t, src32, 0);
-    // deep depths (usually empty) and the top depths (at most 8^2 twigs) each in
-    // one single-block launch; the middle depths one multi-block launch each
-    auto twigs = [&](int d_hi, int d_lo, int b) {
-        if (want_f32) k_moments_twigs_f32<<<b, 256, 0, s>>>(cube, t, d_hi, d_lo);
-        else k_moments_twigs<<<b, 256, 0, s>>>(cube, t, d_hi, d_lo);
-    };
-    twigs(kMaxDepth - 1, 13, 1);
-    for (int d = 12; d >= 3; --d) {
-        int cap = t.twig_off[d + 1] - t.twig_off[d];
-        int b = (cap + 31) / 32;
-        if (b > 4 * 152) b = 4 * 152;
-        twigs(d, d, b < 1 ? 1 : b);
-    }
-    twigs(2, 0, 1);
 }
 
 }  // namespace ucp

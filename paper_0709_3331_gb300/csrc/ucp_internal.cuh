@@ -55,6 +55,7 @@ struct Tree {
     float4* f32;             // kF32 float4 per box
     float* mom32;            // FP32C contexts: 16 floats per box {e xyz, S0, M, D, Q, 0, 0}
     int* child8;             // 8 child slots per box (octant order), -1 = empty
+    int* arrive;             // finished children per box (moments' bottom-up sweep)
     int* leaf_list;          // the leaves, any order
     int* twig_list;          // the twigs of depth d at twig_off[d] .. + count[d]
     int* count;              // count[d] twigs of depth d (d <= 20), count[kMaxDepth + 1] leaves

@@ -488,6 +488,7 @@ int ucp_create_batch(ucp_ctx** out, const ucp_params* p, int32_t n_clouds, const
         (rc = dalloc(c, &c->t.info, cz)) || (rc = dalloc(c, &c->t.depth_leaf, cz)) ||
         (rc = dalloc(c, &c->t.cell, cz)) || (rc = dalloc(c, &c->t.mom, cz * kMom)) ||
         (rc = dalloc(c, &c->t.child8, cz * 8)) || (rc = dalloc(c, &c->t.leaf_list, cz)) ||
+        (rc = dalloc(c, &c->t.arrive, cz)) ||
         (rc = dalloc(c, &c->t.count, kMaxDepth + 2)))
         return bail(rc);
     {
