@@ -90,7 +90,7 @@ k_walk_adjoint(WalkArgs a, const double* __restrict__ lam, double* __restrict__ 
         if (chunk >= a.nchunks) break;
         const int4 ck = a.chunks[chunk];
         const bool valid = lane < ck.y;
-        const int t = valid ? ck.x + lane : -1;
+        const int t = valid ? (a.targets ? a.targets[ck.x + lane] : ck.x + lane) : -1;
         const int root = a.pos_off[a.t.cloud_start ? a.t.cloud_start[ck.z] : 0];
         const int end = info[root].z;
         const double xt = valid ? X[t] : 0.0, yt = valid ? Y[t] : 0.0, zt = valid ? Z[t] : 0.0;
@@ -339,7 +339,7 @@ k_walk_adjoint_f32(WalkArgs a, const double* __restrict__ lam, double* __restric
         if (chunk >= a.nchunks) break;
         const int4 ck = a.chunks[chunk];
         const bool valid = lane < ck.y;
-        const int t = valid ? ck.x + lane : -1;
+        const int t = valid ? (a.targets ? a.targets[ck.x + lane] : ck.x + lane) : -1;
         const int root = a.pos_off[a.t.cloud_start ? a.t.cloud_start[ck.z] : 0];
         const int end = __float_as_int(F[(size_t)root * kF32 + 1].w);
         float xh = 0.f, yh = 0.f, zh = 0.f, xl = 0.f, yl = 0.f, zl = 0.f;
@@ -639,13 +639,12 @@ void launch_ke_seed(const double* v, const int8_t* sp, int n, double me, double*
     k_ke_seed<<<1, 256, 0, s>>>(v, sp, n, me, lam_v, loss);
 }
 
-void launch_walk_adjoint(const WalkArgs& a, const double* lam, double* mu, double* adj, int nn_cap,
+void launch_walk_adjoint(const WalkArgs& a, const double* lam, double* mu, double* adj, int n,
                          int nsm, cudaStream_t s)
 {
     count_launch(3);
-    (void)nn_cap;
     cudaMemsetAsync(a.work, 0, sizeof(int), s);
-    cudaMemsetAsync(mu, 0, sizeof(double) * 3 * (size_t)a.ntargets, s);
+    cudaMemsetAsync(mu, 0, sizeof(double) * 3 * (size_t)n, s);
     int blocks = nsm * 8;
     int need = (a.nchunks + kAdjWarps - 1) / kAdjWarps;
     if (blocks > need) blocks = need;

@@ -139,7 +139,9 @@ void launch_chunk_order(int4* chunks, int nchunks, const int* targets, const int
                         const int* cnt_m2p, float* cost, int4* tmp, cudaStream_t s);
 
 // ---- adjoint (ucp_adjoint.cu) ----
-void launch_walk_adjoint(const WalkArgs& a, const double* lam, double* mu, double* adj, int nn_cap,
+// mu (n particles, key order) = (d a / d x)^T lam over the targets of a (all
+// particles when a.targets is NULL; the others must have lam = 0)
+void launch_walk_adjoint(const WalkArgs& a, const double* lam, double* mu, double* adj, int n,
                          int nsm, cudaStream_t s);
 void launch_gather3(const double* src, const unsigned int* id, int n, double* dst, cudaStream_t s);
 void launch_scatter_add3(const double* src, const unsigned int* id, int n, double* dst,

@@ -1080,17 +1080,28 @@ int ucp_grad_ke_electrons(ucp_ctx* c, double dt_e, int kk, int64_t n_steps, doub
             a.msp = c->msp;
             a.src32 = f32 ? c->src32 : nullptr;  // FP32C: the FP32 adjoint walk
             a.t = c->t;
-            a.targets = nullptr;
-            a.ntargets = c->n;
-            a.chunks = c->chunks_all;
-            a.nchunks = c->n_chunks_all;
+            if (ci == 0.0 && c->n_e > 0) {
+                // inside a block the ions' weights are zero: only the electrons'
+                // accelerations carry adjoint weight, so only they are walked
+                launch_select(c->sp[k], UCP_ELECTRON, c->n, c->tflags, c->tlist, c->scan_part,
+                              c->tcount, c->s);
+                a.targets = c->tlist;
+                a.ntargets = c->n_e;
+                a.chunks = c->chunks_e;
+                a.nchunks = c->n_chunks_e;
+            } else {
+                a.targets = nullptr;
+                a.ntargets = c->n;
+                a.chunks = c->chunks_all;
+                a.nchunks = c->n_chunks_all;
+            }
             a.pos_off = c->pos_off;
             a.eps2 = eps * eps;
             a.kelbg = 0;
             a.lambda = 1.0;
             a.work = c->work;
             a.err = c->sort.err;
-            launch_walk_adjoint(a, lsorted, mu, adj, c->t.cap, c->nsm, c->s);
+            launch_walk_adjoint(a, lsorted, mu, adj, c->n, c->nsm, c->s);
             launch_scatter_add3(mu, c->id[k], c->n, lx, c->s);
             if (g > 0) launch_axpy3(lv, lx, dt_e, c->n, c->s);  // drift g
             if ((rc = check_launch(c, "adjoint"))) break;
@@ -1171,7 +1182,7 @@ int ucp_accel_vjp(ucp_ctx* c, double theta, double eps, const double* lam_in, do
     a.lambda = 1.0;
     a.work = c->work;
     a.err = c->sort.err;
-    launch_walk_adjoint(a, lsorted, mu, adj, c->t.cap, c->nsm, c->s);
+    launch_walk_adjoint(a, lsorted, mu, adj, c->n, c->nsm, c->s);
     launch_scatter_add3(mu, c->id[k], c->n, out, c->s);
     rc = check_launch(c, "adjoint walk");
     cudaMemcpyKind kout = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
