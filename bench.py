@@ -280,8 +280,9 @@ def run_reference(args):
 
 # --------------------------------------------------------------------- GPU arm
 def traffic_record():
-    """Per-launch DRAM bytes of the FP32C walk from the committed ncu summary,
-    valid only while the walk source is unchanged since the capture."""
+    """DRAM bytes per walk launch of a block step (one walk over every particle,
+    nine over the electrons) from the committed ncu summary, valid only while the
+    walk source is unchanged since the capture."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "walk_fp32c_traffic.txt")
     src = os.path.join(ROOT, "paper_0709_3331_gb300", "csrc", "ucp_walk.cu")
@@ -296,9 +297,11 @@ def traffic_record():
     if rec.get("walk_source_sha256_16") != h:
         return None
     try:
-        return float(rec["dram_bytes_per_full_launch"])
+        full = float(rec["dram_bytes_per_full_walk"])
+        elec = float(rec["dram_bytes_per_electron_walk"])
     except (KeyError, ValueError):
         return None
+    return (full + (WORKLOAD["k"] - 1) * elec) / WORKLOAD["k"]
 
 
 def run_gpu(args):
