@@ -378,7 +378,7 @@ k_walk_adjoint_f32(WalkArgs a, const double* __restrict__ lam, double* __restric
                     if (in && j != t) {
                         float r3[3] = {rx + (odd ? P.y : P.x), ry + (odd ? P.w : P.z),
                                        rz + (odd ? Q.y : Q.x)};
-                        float g = rsqrtf(dot3f(r3, r3) + eps2);
+                        float g = rsqrt_ftz(dot3f(r3, r3) + eps2);
                         float g3 = g * g * g, g5 = g3 * g * g;
                         float rl = dot3f(r3, l), rw = dot3f(r3, wv);
 #pragma unroll
@@ -443,7 +443,7 @@ k_walk_adjoint_f32(WalkArgs a, const double* __restrict__ lam, double* __restric
                     const float M = C.z;
                     const float D[3] = {C.w, D4.x, D4.y};
                     const float Q[6] = {D4.z, D4.w, E4.x, E4.y, E4.z, E4.w};
-                    const float g = rsqrtf(d2 + eps2);
+                    const float g = rsqrt_ftz(d2 + eps2);
                     const float g2 = g * g, g3 = g2 * g, g5 = g3 * g2, g7 = g5 * g2, g9 = g7 * g2;
                     const float Rl = dot3f(R, l), RD = dot3f(R, D), lD = dot3f(l, D);
                     const float Rw = dot3f(R, wv);

@@ -25,6 +25,18 @@ __device__ __forceinline__ double unord64(unsigned long long u)
     return __longlong_as_double((long long)((u >> 63) ? (u & 0x7fffffffffffffffull) : ~u));
 }
 
+// Approximate reciprocal square root of the special-function unit (the
+// approximation rsqrtf uses) with subnormal inputs and outputs flushed to zero,
+// which spares the subnormal handling around it.  The walks call it on r^2 + eps^2
+// or on |x_t - c|^2 + eps^2: below 2^-126 only for particles closer than 1e-19, whose
+// FP32 field overflows in any case; for every normal input the result is rsqrtf's.
+__device__ __forceinline__ float rsqrt_ftz(float x)
+{
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 // Kernels launched by this process (read by ucp_stats).
 extern std::atomic<unsigned long long> g_launches;
 inline void count_launch(int k) { g_launches.fetch_add((unsigned long long)k, std::memory_order_relaxed); }

@@ -127,7 +127,7 @@ __device__ __forceinline__ void m2p_f32(float rx, float ry, float rz, float r2, 
                                         float Qxz, float Qyy, float Qyz, float Qzz, float& ex,
                                         float& ey, float& ez, float& ph)
 {
-    float g = rsqrtf(r2);
+    float g = rsqrt_ftz(r2);
     float u = g * g;
     float g3 = g * u;
     float QRx = fmaf(Qxx, rx, fmaf(Qxy, ry, Qxz * rz));
@@ -394,7 +394,7 @@ k_walk_fp32c(WalkArgs a)
                 float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __ffma2_rn(dz, dz, e2)));
                 const bool ok0 = j >= jb && j != t;
                 const bool ok1 = j + 1 < je && j + 1 != t;
-                float2 ri = make_float2(ok0 ? rsqrtf(r2.x) : 0.f, ok1 ? rsqrtf(r2.y) : 0.f);
+                float2 ri = make_float2(ok0 ? rsqrt_ftz(r2.x) : 0.f, ok1 ? rsqrt_ftz(r2.y) : 0.f);
                 float2 qi = __fmul2_rn(make_float2(Q.z, Q.w), ri);
                 float2 qr3 = __fmul2_rn(__fmul2_rn(qi, ri), ri);
                 px = __ffma2_rn(qr3, dx, px);
@@ -514,7 +514,7 @@ k_walk_fp32c(WalkArgs a)
                                 pp = fmaf(qj * inv_lambda, pf, pp);
                             } else {
                                 float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
-                                float ri = rsqrtf(r2);
+                                float ri = rsqrt_ftz(r2);
                                 float qi = qj * ri;
                                 float qr3 = qi * ri * ri;
                                 px = fmaf(qr3, dx, px);
@@ -545,7 +545,7 @@ k_walk_fp32c(WalkArgs a)
                         float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __ffma2_rn(dz, dz, e2)));
                         const bool ok0 = j >= jb && j != t;
                         const bool ok1 = j + 1 < je && j + 1 != t;
-                        float2 ri = make_float2(ok0 ? rsqrtf(r2.x) : 0.f, ok1 ? rsqrtf(r2.y) : 0.f);
+                        float2 ri = make_float2(ok0 ? rsqrt_ftz(r2.x) : 0.f, ok1 ? rsqrt_ftz(r2.y) : 0.f);
                         float2 qi = __fmul2_rn(make_float2(Q.z, Q.w), ri);
                         float2 qr3 = __fmul2_rn(__fmul2_rn(qi, ri), ri);
                         px = __ffma2_rn(qr3, dx, px);
