@@ -788,23 +788,26 @@ __device__ __forceinline__ void finish_box_f32(const float* a, const double z[3]
     m64[MDELTA] = sqrtf(fmaf(e[0], e[0], fmaf(e[1], e[1], e[2] * e[2])));
 }
 
-// Child slot o of twig p shifted to the twig's centre zp (zeros for an empty slot).
-__device__ __forceinline__ void twig_child_f32(const Tree& t, int p, int o, const double zp[3],
-                                               float* a)
+// Child slot o of twig p shifted to the twig's centre (zeros for an empty slot).
+// The child's expansion centre lies at its own geometric centre plus its FP32
+// offset e_child (mom32), and its geometric centre at the twig's plus q = side/4
+// along each axis, signed by the octant bit (x bit 0, y bit 1, z bit 2): the shift
+// is q +/- e_child, formed in FP32 without touching the FP64 unit.
+__device__ __forceinline__ void twig_child_f32(const Tree& t, int p, int o, float q, float* a)
 {
 #pragma unroll
     for (int k = 0; k < 14; ++k) a[k] = 0.f;
     const int ch = t.child8[(size_t)p * 8 + o];
     if (ch < 0) return;
-    const double* cm = t.mom + (size_t)ch * kMom;
     const float4* r32 = reinterpret_cast<const float4*>(t.mom32 + (size_t)ch * 16);
     const float4 R0 = __ldcg(r32), R1 = __ldcg(r32 + 1), R2 = __ldcg(r32 + 2),
                  R3 = __ldcg(r32 + 3);
     const float S0k = R0.w, Mk = R1.x;
     const float dk[3] = {R1.y, R1.z, R1.w};
     const float qk[6] = {R2.x, R2.y, R2.z, R2.w, R3.x, R3.y};
+    const float ec[3] = {R0.x, R0.y, R0.z};
     float e[3];
-    for (int k = 0; k < 3; ++k) e[k] = (float)(__ldcg(cm + MC + k) - zp[k]);
+    for (int k = 0; k < 3; ++k) e[k] = ((o >> k) & 1 ? q : -q) + ec[k];
     a[0] = S0k;
     a[1] = Mk;
     for (int k = 0; k < 3; ++k) {
@@ -828,13 +831,14 @@ __device__ void twig_combine_f32(const Cube* __restrict__ cube, const Tree& t, i
     const Cube cb = cube_of(cube, t, t.info[p].x);
     double zp[3], ps;
     box_centre(cb, t.cell[p], d, zp, &ps);
+    const float q = (float)(0.25 * ps);
     float u[14], v[14], w[14];
     const int order[4][2] = {{0, 4}, {2, 6}, {1, 5}, {3, 7}};
 #pragma unroll 1
     for (int g = 0; g < 4; ++g) {
         float b0[14], b1[14];
-        twig_child_f32(t, p, order[g][0], zp, b0);
-        twig_child_f32(t, p, order[g][1], zp, b1);
+        twig_child_f32(t, p, order[g][0], q, b0);
+        twig_child_f32(t, p, order[g][1], q, b1);
 #pragma unroll
         for (int k = 0; k < 14; ++k) {
             const float s = b0[k] + b1[k];
