@@ -424,7 +424,8 @@ def run_gpu(args):
     extra = {}
     if not args.quick:
         extra = run_extras(c, W, ws, pos_d, vel_d, sp_d, Context, UCP_FP32C, UCP_FP64,
-                           timed_steps, flush, stream, peak, ms / args.steps, tl, gpu_samples)
+                           timed_steps, flush, stream, peak, ms / args.steps, tl, gpu_samples,
+                           mpk)
 
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -537,7 +538,7 @@ def run_e2e(c, W, args, ws, dev, flush, Context, UCP_FP32C):
 
 
 def run_extras(c, W, ws, pos_d, vel_d, sp_d, Context, UCP_FP32C, UCP_FP64, timed_steps, flush,
-               stream, peak, ms_step32, tl, gpu_samples):
+               stream, peak, ms_step32, tl, gpu_samples, mpk):
     import torch
     extra = {}
     ctx64 = Context(c.n, c.q, c.m, leaf_cap=W["leaf_cap"], precision=UCP_FP64)
@@ -547,9 +548,14 @@ def run_extras(c, W, ws, pos_d, vel_d, sp_d, Context, UCP_FP32C, UCP_FP64, timed
     ctx64.step(W["dt_e"], W["k"], W["k"], W["theta"], W["eps"])
     torch.cuda.synchronize()
     ms64, st64, wms64, wn64, _ = timed_steps(ctx64, 1)
+    fl64 = FLOP_P2P * float(st64[0]) + FLOP_M2P * float(st64[1])
     extra["fp64"] = {"value": float(st64[0] + st64[1]) / (ms64 / 1e3), "unit": UNIT,
                      "ms_per_step": ms64, "walk_ms_per_launch": wms64 / max(wn64, 1),
-                     "speedup_fp32c_over_fp64": ms64 / ms_step32}
+                     "speedup_fp32c_over_fp64": ms64 / ms_step32,
+                     "walk_frac_fp64_peak": fl64 / (wms64 / 1e3) / 1e12 / mpk["fp64_fma_tflops"]
+                     if wms64 > 0 else None,
+                     "note": "walk_frac_fp64_peak: the same flop counts over the FP64 FMA rate "
+                             "measured on this GPU (ucp_measure_peaks)"}
     ctx64.close()
     sweep = {}
     for th in (0.3, 0.5, 0.7):
