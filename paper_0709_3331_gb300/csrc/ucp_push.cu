@@ -139,13 +139,17 @@ __global__ void k_energy_clouds(const double* __restrict__ vx, const double* __r
     if (threadIdx.x < 6) out[6 * c + threadIdx.x] = sh[0][threadIdx.x];
 }
 
-__global__ void k_energy_final(const double* __restrict__ part, int nblk, double* __restrict__ out)
+// Six warps, one per observable: lane l adds partials l, l + 32, ..., then the
+// lanes are added by a fixed butterfly (a deterministic order).
+__global__ void __launch_bounds__(192)
+k_energy_final(const double* __restrict__ part, int nblk, double* __restrict__ out)
 {
-    if (threadIdx.x != 0) return;
-    double acc[6] = {0, 0, 0, 0, 0, 0};
-    for (int b = 0; b < nblk; ++b)
-        for (int k = 0; k < 6; ++k) acc[k] += part[6 * b + k];
-    for (int k = 0; k < 6; ++k) out[k] = acc[k];
+    const int k = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    double acc = 0.0;
+    for (int b = lane; b < nblk; b += 32) acc += part[6 * b + k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) out[k] = acc;
 }
 
 __global__ void k_scatter3(const double* __restrict__ ax, const double* __restrict__ ay,
@@ -248,7 +252,7 @@ void launch_energy(const double* vx, const double* vy, const double* vz, const d
 {
     count_launch(2);
     k_energy_partial<<<nblk, kT, 0, s>>>(vx, vy, vz, phi, sp, qsp, msp, n, partials);
-    k_energy_final<<<1, 32, 0, s>>>(partials, nblk, out6);
+    k_energy_final<<<1, 192, 0, s>>>(partials, nblk, out6);
 }
 
 void launch_energy_clouds(const double* vx, const double* vy, const double* vz, const double* phi,
