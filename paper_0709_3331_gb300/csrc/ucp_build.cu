@@ -501,6 +501,73 @@ __global__ void k_topo_count(const unsigned long long* __restrict__ K, int n, in
     cnt[i] = c;
 }
 
+// ---- the same counts by a window of sorted positions (leaf_cap <= kTopoWin).
+// fd[j] = first_depth(j): the box of depth d that holds position i ends at the
+// first j > i with fd[j] <= d and starts at the last j <= i with fd[j] <= d.  It
+// holds at most leaf_cap particles iff those two lie within leaf_cap of each
+// other, so the depth of the leaf that holds i is
+//   min over m = 0 .. leaf_cap - 1 of max(min fd[i - m .. i], min fd[i + 1 .. i + leaf_cap - m])
+// (capped at kMaxDepth): a fixed window of shared memory instead of searches.
+// Outside [0, n) and at every segment start fd is 0, which closes every box.
+constexpr int kTopoThreads = 256;
+constexpr int kTopoWin = 32;
+
+__device__ __forceinline__ int fd_at(const unsigned long long* __restrict__ K, const Tree& t,
+                                     int n, int j)
+{
+    if (j <= 0 || j >= n) return 0;
+    int lo, hi;
+    segment_of(t, n, j, lo, hi);
+    return first_depth(K, lo, j);
+}
+
+// fd over [base - kTopoWin, base + kTopoThreads + kTopoWin) into smem
+__device__ __forceinline__ void load_fd_window(const unsigned long long* __restrict__ K,
+                                               const Tree& t, int n, int base,
+                                               unsigned char* fd)
+{
+    for (int k = threadIdx.x; k < kTopoThreads + 2 * kTopoWin; k += kTopoThreads)
+        fd[k] = (unsigned char)fd_at(K, t, n, base - kTopoWin + k);
+}
+
+// depth of the leaf that holds the position in slot li (see above)
+__device__ __forceinline__ int leaf_depth_win(const unsigned char* fd, int li, int w,
+                                              unsigned char* bmin)
+{
+    int bm = 255;
+    for (int m = 0; m < w; ++m) {
+        bm = min(bm, (int)fd[li - m]);
+        bmin[m] = (unsigned char)bm;
+    }
+    int fm = 255, best = 255;
+    for (int m = w - 1; m >= 0; --m) {
+        fm = min(fm, (int)fd[li + (w - m)]);
+        best = min(best, max((int)bmin[m], fm));
+    }
+    return min(best, kMaxDepth);
+}
+
+__global__ void __launch_bounds__(kTopoThreads)
+k_topo_count_win(const unsigned long long* __restrict__ K, int n, int leaf_cap,
+                 int* __restrict__ cnt, Tree t)
+{
+    __shared__ unsigned char fd[kTopoThreads + 2 * kTopoWin];
+    __shared__ unsigned char bmin[kTopoThreads][kTopoWin];
+    const int base = blockIdx.x * kTopoThreads;
+    load_fd_window(K, t, n, base, fd);
+    __syncthreads();
+    const int i = base + threadIdx.x;
+    if (i >= n) return;
+    const int li = threadIdx.x + kTopoWin;
+    const int d0 = fd[li];
+    int c = 0;
+    if (d0 <= kMaxDepth) {
+        const int lv = leaf_depth_win(fd, li, leaf_cap, bmin[threadIdx.x]);
+        if (lv >= d0) c = lv - d0 + 1;
+    }
+    cnt[i] = c;
+}
+
 // atomicAdd(ctr, 1) for every calling lane, one atomic per distinct counter in
 // the warp (the lanes that add to the same counter take consecutive slots)
 __device__ __forceinline__ int warp_inc(int* ctr)
@@ -514,9 +581,18 @@ __device__ __forceinline__ int warp_inc(int* ctr)
     return base + __popc(peers & ((1u << lane) - 1u));
 }
 
-__global__ void k_topo_emit(const unsigned long long* __restrict__ K, int n, int leaf_cap,
-                            const int* __restrict__ cnt, const int* __restrict__ off, Tree t)
+template <bool kWin>
+__global__ void __launch_bounds__(kTopoThreads)
+k_topo_emit(const unsigned long long* __restrict__ K, int n, int leaf_cap,
+            const int* __restrict__ cnt, const int* __restrict__ off, Tree t)
 {
+    // with kWin the leaf's end comes from the window of first depths (a leaf
+    // holds at most leaf_cap <= kTopoWin positions unless it is a depth-cap box)
+    __shared__ unsigned char fd[kWin ? kTopoThreads + 2 * kTopoWin : 1];
+    if (kWin) {
+        load_fd_window(K, t, n, blockIdx.x * kTopoThreads, fd);
+        __syncthreads();
+    }
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     int c = cnt[i];
@@ -536,7 +612,14 @@ __global__ void k_topo_emit(const unsigned long long* __restrict__ K, int n, int
     int dmax = 0;
     for (int j = 0; j < c; ++j) {
         int d = d0 + j;
-        int e = box_end(K, hi, i, d);
+        int e = -1;
+        if (kWin && j == c - 1) {
+            // the leaf: its end within the window, else (a bigger depth-cap box) search
+            const int li = threadIdx.x + kTopoWin;
+            for (int m = 1; m <= leaf_cap && e < 0; ++m)
+                if (fd[li + m] <= d) e = i + m;
+        }
+        if (e < 0) e = box_end(K, hi, i, d);
         bool leaf = (e - i <= leaf_cap) || d == kMaxDepth;
         int nx = e < n ? off[e] : nn;
         if (node >= t.cap) break;  // cannot happen: the capacity bounds the box count
@@ -1025,10 +1108,14 @@ void launch_topology(const unsigned long long* key, int n, int leaf_cap, int* po
     count_launch(3);
     cudaMemsetAsync(t.maxdepth, 0, sizeof(int), s);
     cudaMemsetAsync(t.count, 0, sizeof(int) * (kMaxDepth + 2), s);
-    k_topo_count<<<(n + 255) / 256, 256, 0, s>>>(key, n, leaf_cap, pos_cnt, t);
+    const int nb = (n + kTopoThreads - 1) / kTopoThreads;
+    const bool win = leaf_cap <= kTopoWin;
+    if (win) k_topo_count_win<<<nb, kTopoThreads, 0, s>>>(key, n, leaf_cap, pos_cnt, t);
+    else k_topo_count<<<nb, kTopoThreads, 0, s>>>(key, n, leaf_cap, pos_cnt, t);
     launch_scan(pos_cnt, pos_off, n, scan_part, t.nnodes, s);
     k_clear_children<<<2 * 152, 256, 0, s>>>(t);
-    k_topo_emit<<<(n + 255) / 256, 256, 0, s>>>(key, n, leaf_cap, pos_cnt, pos_off, t);
+    if (win) k_topo_emit<true><<<nb, kTopoThreads, 0, s>>>(key, n, leaf_cap, pos_cnt, pos_off, t);
+    else k_topo_emit<false><<<nb, kTopoThreads, 0, s>>>(key, n, leaf_cap, pos_cnt, pos_off, t);
 }
 
 void launch_moments(const double* x, const double* y, const double* z, const int8_t* sp,
