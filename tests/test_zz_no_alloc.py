@@ -61,6 +61,15 @@ def test_root_cube_static_matches_tree_build(orc):
             ref = ctx.get_cube()
         assert got.tobytes() == ref.tobytes()          # bit for bit, zero signs included
         np.testing.assert_array_equal(got, orc.root_cube(pos_np))
+    # exactly the largest size the fixed scratch holds (every one of its 1024 tile slots)
+    big = gaussian_cloud(UCP_STATIC_MAX_N, 8.0, 11)
+    got, _, _ = _static_cube(torch, f, big.pos, stream)
+    with Context(big.n, big.q, big.m, leaf_cap=16) as ctx:
+        ctx.set_state(big.pos, big.vel, big.species)
+        ctx.tree_build()
+        ref = ctx.get_cube()
+    assert got.tobytes() == ref.tobytes()
+    np.testing.assert_array_equal(got, orc.root_cube(big.pos))
     # a NaN coordinate: the library refuses such a state; here the axis's centre is NaN
     bad = gaussian_cloud(1000, 1.0, 9).pos.copy()
     bad[17, 1] = np.nan
