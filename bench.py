@@ -6,7 +6,7 @@ dt_e = 1e-3 (each: kick, drift, tree build, walk over the electrons; the tenth
 walks every particle), the ion kicks, and the energy/momentum reduction.
 Workload: N = 524,288 (262,144 ions, 262,144 electrons), Gaussian cloud
 sigma = 8, m_i/m_e = 1000, T_e = 1, T_i = 0.01, eps = 0.01, theta = 0.5,
-leaf_cap = 16, FP32 node-relative walk with compensated sums and FP64 state.
+leaf_cap = 32, FP32 node-relative walk with compensated sums and FP64 state.
 
 Prints one JSON line.  ``value`` = tree-force interactions/s (direct pairs +
 multipole evaluations) over the timed steps, device-timed with CUDA events on
@@ -35,7 +35,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOAD = dict(name="precision_n524288", n=524288, sigma=8.0, seed=3, theta=0.5, eps=0.01,
-                leaf_cap=16, dt_e=1e-3, k=10)
+                leaf_cap=32, dt_e=1e-3, k=10)
 METRIC = "tree-force interactions/s at N=524288 (FP32 compensated walk, FP64 state)"
 UNIT = "interactions/s"
 # Flops charged per interaction by the roofline (counted from the FP32C kernel's
@@ -282,7 +282,7 @@ def run_reference(args):
 def traffic_record():
     """DRAM bytes per walk launch of a block step (one walk over every particle,
     nine over the electrons) from the committed ncu summary, valid only while the
-    walk source is unchanged since the capture."""
+    walk source and the leaf population are those of the capture."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "walk_fp32c_traffic.txt")
     src = os.path.join(ROOT, "paper_0709_3331_gb300", "csrc", "ucp_walk.cu")
@@ -294,7 +294,7 @@ def traffic_record():
         if ":" in line:
             k, v = line.split(":", 1)
             rec[k.strip()] = v.strip()
-    if rec.get("walk_source_sha256_16") != h:
+    if rec.get("walk_source_sha256_16") != h or rec.get("leaf_cap") != str(WORKLOAD["leaf_cap"]):
         return None
     try:
         full = float(rec["dram_bytes_per_full_walk"])
@@ -816,10 +816,14 @@ def main():
     ap.add_argument("--n", type=int, default=0, help="profile case: override the particle count")
     ap.add_argument("--precision", default="fp32c", choices=["fp32c", "fp64"])
     ap.add_argument("--theta", type=float, default=0.5)
-    ap.add_argument("--leaf-cap", type=int, default=16)
+    ap.add_argument("--leaf-cap", type=int, default=None,
+                    help="largest leaf population (default: the workload's)")
     ap.add_argument("--repeat", type=int, default=1)
     ap.add_argument("--shape", type=int, default=0, help="profile case: FP32C walk launch shape")
     args = ap.parse_args()
+    if args.leaf_cap is None:
+        args.leaf_cap = WORKLOAD["leaf_cap"]
+    WORKLOAD["leaf_cap"] = args.leaf_cap
     if args.profile_case:
         return run_profile_case(args)
     if args.warmup < 3 and args.impl == "gpu":

@@ -238,6 +238,7 @@ constexpr int kSortChunks = 8;                              // 32-key chunks per
 constexpr int kSortTile = kSortThreads * kSortChunks;       // 2048 keys per block
 constexpr int kRadix = 256;
 constexpr int kSortSpinLimit = 1 << 20;  // polls of a predecessor's word before giving up
+constexpr int kLook = 8;                  // predecessors read per look-back round trip
 
 // Digit histograms of all eight passes in one read of the keys.
 __global__ void __launch_bounds__(kSortThreads)
@@ -342,22 +343,40 @@ k_onesweep(const unsigned long long* __restrict__ kin, const unsigned int* __res
         unsigned int prefix = 0;
         if (tile > 0) {
             atomicExch(mine, tag | (1ull << 32) | (unsigned int)total);
+            // kLook predecessors' words per round trip (independent loads), taken in
+            // order j, j - 1, ... up to the first inclusive prefix or the first word
+            // not yet published, which is polled again
             int j = tile - 1, spins = 0;
-            while (j >= 0) {
-                unsigned long long v = __ldcv(status + (size_t)j * kRadix + d);
-                unsigned int flag = (unsigned int)(v >> 32) & 3u;
-                if ((v >> 34) != (unsigned long long)epoch || flag == 0u) {
+            bool done = false;
+            while (!done) {
+                unsigned long long v[kLook];
+#pragma unroll
+                for (int u = 0; u < kLook; ++u)
+                    v[u] = j - u >= 0 ? __ldcv(status + (size_t)(j - u) * kRadix + d) : 0ull;
+                int used = 0;
+                bool blocked = false;
+#pragma unroll
+                for (int u = 0; u < kLook; ++u) {
+                    if (done || blocked || j - u < 0) continue;
+                    const unsigned int flag = (unsigned int)(v[u] >> 32) & 3u;
+                    if ((v[u] >> 34) != (unsigned long long)epoch || flag == 0u) {
+                        blocked = true;
+                        continue;
+                    }
+                    prefix += (unsigned int)v[u];
+                    ++used;
+                    if (flag == 2u) done = true;
+                }
+                j -= used;
+                if (done || j < 0) break;  // (tile 0 publishes an inclusive prefix)
+                if (blocked) {
                     if (++spins > spin_limit) {
                         atomicOr(err, 1);
                         s_fail = 1;
                         break;
                     }
                     __nanosleep(64);
-                    continue;
                 }
-                prefix += (unsigned int)v;
-                if (flag == 2u) break;
-                --j;
             }
         }
         atomicExch(mine, tag | (2ull << 32) | (prefix + (unsigned int)total));
@@ -530,19 +549,24 @@ __device__ __forceinline__ void load_fd_window(const unsigned long long* __restr
         fd[k] = (unsigned char)fd_at(K, t, n, base - kTopoWin + k);
 }
 
-// depth of the leaf that holds the position in slot li (see above)
-__device__ __forceinline__ int leaf_depth_win(const unsigned char* fd, int li, int w,
-                                              unsigned char* bmin)
+// depth of the leaf that holds the position in slot li (see above); the
+// backward running minima stay in registers (fully unrolled over the window)
+__device__ __forceinline__ int leaf_depth_win(const unsigned char* fd, int li, int w)
 {
+    int bmin[kTopoWin];
     int bm = 255;
-    for (int m = 0; m < w; ++m) {
-        bm = min(bm, (int)fd[li - m]);
-        bmin[m] = (unsigned char)bm;
+#pragma unroll
+    for (int m = 0; m < kTopoWin; ++m) {
+        if (m < w) bm = min(bm, (int)fd[li - m]);
+        bmin[m] = bm;
     }
     int fm = 255, best = 255;
-    for (int m = w - 1; m >= 0; --m) {
-        fm = min(fm, (int)fd[li + (w - m)]);
-        best = min(best, max((int)bmin[m], fm));
+#pragma unroll
+    for (int m = kTopoWin - 1; m >= 0; --m) {
+        if (m < w) {
+            fm = min(fm, (int)fd[li + (w - m)]);
+            best = min(best, max(bmin[m], fm));
+        }
     }
     return min(best, kMaxDepth);
 }
@@ -552,7 +576,6 @@ k_topo_count_win(const unsigned long long* __restrict__ K, int n, int leaf_cap,
                  int* __restrict__ cnt, Tree t)
 {
     __shared__ unsigned char fd[kTopoThreads + 2 * kTopoWin];
-    __shared__ unsigned char bmin[kTopoThreads][kTopoWin];
     const int base = blockIdx.x * kTopoThreads;
     load_fd_window(K, t, n, base, fd);
     __syncthreads();
@@ -562,7 +585,7 @@ k_topo_count_win(const unsigned long long* __restrict__ K, int n, int leaf_cap,
     const int d0 = fd[li];
     int c = 0;
     if (d0 <= kMaxDepth) {
-        const int lv = leaf_depth_win(fd, li, leaf_cap, bmin[threadIdx.x]);
+        const int lv = leaf_depth_win(fd, li, leaf_cap);
         if (lv >= d0) c = lv - d0 + 1;
     }
     cnt[i] = c;
@@ -755,6 +778,21 @@ __device__ void twig_combine_f64(const Cube* __restrict__ cube, const Tree& t, i
     for (int k = 0; k < kMom; ++k) pm[k] = rec[k];
 }
 
+constexpr int kMomThreads = 64;  // threads per block of the leaf kernels
+
+// atomicAdd with acquire-release semantics at device scope: the caller's
+// earlier writes are visible to whoever reads the counter after it (release),
+// and the writes released by every earlier increment of the counter are
+// visible to the caller after it (acquire: the increments form one release
+// sequence).  One ordered atomic in place of a fence on either side.
+__device__ __forceinline__ int atomic_add_acq_rel(int* ctr, int v)
+{
+    int old;
+    asm volatile("atom.acq_rel.gpu.global.add.s32 %0, [%1], %2;"
+                 : "=r"(old) : "l"(ctr), "r"(v) : "memory");
+    return old;
+}
+
 // Bottom-up sweep from a finished box: each box counts its finished children
 // (t.arrive, zeroed before the launch); the thread that finishes the last child
 // combines the parent and carries on upwards.  No thread waits for another, and
@@ -767,9 +805,9 @@ __device__ __forceinline__ void sweep_up(const Tree& t, int node, Combine combin
         int nch = 0;
 #pragma unroll
         for (int o = 0; o < 8; ++o) nch += t.child8[(size_t)p * 8 + o] >= 0;
-        __threadfence();  // this box's records before its arrival is counted
-        if (atomicAdd(&t.arrive[p], 1) + 1 < nch) return;
-        __threadfence();  // the other children's records before they are read
+        // this box's records are published with its arrival; the last arrival
+        // sees every sibling's
+        if (atomic_add_acq_rel(&t.arrive[p], 1) + 1 < nch) return;
         combine(p, t.depth_leaf[p] & 255);
         p = t.info[p].w;
     }
@@ -777,7 +815,7 @@ __device__ __forceinline__ void sweep_up(const Tree& t, int node, Combine combin
 
 // Moments of every leaf from its particles, one thread per leaf, summed about
 // the leaf's geometric centre in key order.
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(kMomThreads)
 k_moments_leaves(const double* __restrict__ x, const double* __restrict__ y,
                  const double* __restrict__ z, const int8_t* __restrict__ sp,
                  const double* __restrict__ qsp, const Cube* __restrict__ cube, Tree t,
@@ -942,7 +980,7 @@ __device__ void twig_combine_f32(const Cube* __restrict__ cube, const Tree& t, i
 
 // Leaves, one thread per leaf (full lanes for the FP64 offsets), then the
 // bottom-up sweep over the twigs (sweep_up).
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(kMomThreads)
 k_moments_leaves_f32(const double* __restrict__ x, const double* __restrict__ y,
                      const double* __restrict__ z, const int8_t* __restrict__ sp,
                      const double* __restrict__ qsp, const Cube* __restrict__ cube, Tree t,
@@ -1126,13 +1164,15 @@ void launch_moments(const double* x, const double* y, const double* z, const int
     // (bottom-up sweep with arrival counters), in one launch
     count_launch(1);
     cudaMemsetAsync(t.arrive, 0, sizeof(int) * (size_t)t.cap, s);
-    int blocks = (n + 255) / 256;
-    if (blocks > 4 * 152) blocks = 4 * 152;
+    // small blocks spread the leaf threads (about one per eight particles) evenly
+    // over the SMs
+    int blocks = (n + kMomThreads - 1) / kMomThreads;
+    if (blocks > 16 * 152) blocks = 16 * 152;
     if (blocks < 1) blocks = 1;
     if (want_f32)
-        k_moments_leaves_f32<<<blocks, 256, 0, s>>>(x, y, z, sp, qsp, cube, t, src32);
+        k_moments_leaves_f32<<<blocks, kMomThreads, 0, s>>>(x, y, z, sp, qsp, cube, t, src32);
     else
-        k_moments_leaves<<<blocks, 256, 0, s>>>(x, y, z, sp, qsp, cube, t, src32, 0);
+        k_moments_leaves<<<blocks, kMomThreads, 0, s>>>(x, y, z, sp, qsp, cube, t, src32, 0);
 }
 
 }  // namespace ucp

@@ -144,7 +144,7 @@ def _ptr(a, dtype):
 class Context:
     """One particle set on the current CUDA device (``ucp_create`` .. ``ucp_destroy``)."""
 
-    def __init__(self, n, q=(1.0, -1.0), m=(1000.0, 1.0), leaf_cap=16, precision=UCP_FP64,
+    def __init__(self, n, q=(1.0, -1.0), m=(1000.0, 1.0), leaf_cap=32, precision=UCP_FP64,
                  stream=None, kelbg_lambda=None, sizes=None):
         """``sizes``: particle counts of an ensemble of independent clouds
         (``ucp_create_batch``); their total must equal ``n``."""

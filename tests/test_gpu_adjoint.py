@@ -182,12 +182,12 @@ def _c4():
 
 def test_gradient_fullsize_checkpoints(U):
     """The differentiation workload at its own size (N = 262,144, sigma 6, theta
-    0.5, eps 0.01, leaf_cap 16, FP32C forces with FP64 state, dt_e 1e-3, k = 10):
+    0.5, eps 0.01, leaf_cap 32, FP32C forces with FP64 state, dt_e 1e-3, k = 10):
     over 40 electron substeps, a checkpoint every 20 substeps (forward
     recomputation of each segment) gives the gradient of one unsegmented pass, up
     to the rounding of the adjoint walk's atomic sums."""
     c = _c4()
-    theta, eps, lc, dt, k, steps = 0.5, 0.01, 16, 1e-3, 10, 40
+    theta, eps, lc, dt, k, steps = 0.5, 0.01, 32, 1e-3, 10, 40
     with U.Context(c.n, c.q, c.m, leaf_cap=lc, precision=1) as ctx:
         ctx.set_state(c.pos, c.vel, c.species)
         L, gx, gv = ctx.grad_ke_electrons(dt, k, steps, theta, eps, 20)
@@ -208,7 +208,7 @@ def test_gradient_fullsize_finite_differences(U):
     coordinates are counted, and most coordinates must agree to 1e-3."""
     import torch
     c = _c4()
-    theta, eps, lc, dt, k, steps, h = 0.5, 0.01, 16, 1e-3, 10, 20, 1e-4
+    theta, eps, lc, dt, k, steps, h = 0.5, 0.01, 32, 1e-3, 10, 20, 1e-4
     dev = torch.device("cuda")
     with U.Context(c.n, c.q, c.m, leaf_cap=lc, precision=1) as ctx:
         ctx.set_state(c.pos, c.vel, c.species)

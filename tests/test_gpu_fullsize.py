@@ -1,4 +1,4 @@
-"""Parity at full size: N = 524,288 (sigma 8, leaf_cap 16, eps 0.01, dt_e 1e-3,
+"""Parity at full size: N = 524,288 (sigma 8, leaf_cap 32, eps 0.01, dt_e 1e-3,
 k = 10), the precision workload the benchmark times, in the walk launch shape
 the autotuner picks for it.  The oracle computes sampled targets one by one on
 the GPU's own state, at electron steps 0, 50 and 100 of the split-step run, and
@@ -16,6 +16,7 @@ pytestmark = pytest.mark.gpu
 
 FP64_TOL = 1e-5
 FP32C_TOL = 1e-4
+LEAF_CAP = 32  # the benchmark's leaf population
 NTHREADS = max(1, min(16, os.cpu_count() or 1))
 
 
@@ -46,7 +47,7 @@ def _sample(n, k, seed):
 
 
 def _oracle(orc, pos, c, theta, tl):
-    T = orc.Tree(pos, c.species, c.q, leaf_cap=16)
+    T = orc.Tree(pos, c.species, c.q, leaf_cap=LEAF_CAP)
     E, phi, npp, nmp = T.force(theta, 0.01, targets=tl, nthreads=NTHREADS, counts=True)
     qm = (c.q[c.species[tl]] / c.m[c.species[tl]])[:, None]
     return E * qm, phi, npp, nmp
@@ -69,7 +70,7 @@ def test_fullsize_fp32c_steps_0_50_100(U, orc, cloud):
     keep a force within the tree's own per-target error against the direct sum."""
     c = cloud
     tl = _sample(c.n, 8192, 50)
-    with U.Context(c.n, c.q, c.m, leaf_cap=16, precision=U.UCP_FP32C) as ctx:
+    with U.Context(c.n, c.q, c.m, leaf_cap=LEAF_CAP, precision=U.UCP_FP32C) as ctx:
         ctx.set_state(c.pos, c.vel, c.species)
         ctx.autotune(0.5, 0.01)
         for step in (0, 50, 100):
@@ -99,7 +100,7 @@ def test_fullsize_fp32c_steps_0_50_100(U, orc, cloud):
 def test_fullsize_theta(U, orc, cloud, prec, theta):
     c = cloud
     tl = _sample(c.n, 2048, 7)
-    with U.Context(c.n, c.q, c.m, leaf_cap=16, precision=prec) as ctx:
+    with U.Context(c.n, c.q, c.m, leaf_cap=LEAF_CAP, precision=prec) as ctx:
         ctx.set_state(c.pos, c.vel, c.species)
         if prec == U.UCP_FP32C:
             ctx.autotune(theta, 0.01)
@@ -119,7 +120,7 @@ def test_fullsize_tree_error_vs_direct(U, orc, cloud, theta):
     GPU's error against the direct sum is the oracle tree's, to FP32 rounding."""
     c = cloud
     tl = _sample(c.n, 8192, 99)
-    with U.Context(c.n, c.q, c.m, leaf_cap=16, precision=U.UCP_FP32C) as ctx:
+    with U.Context(c.n, c.q, c.m, leaf_cap=LEAF_CAP, precision=U.UCP_FP32C) as ctx:
         ctx.set_state(c.pos, c.vel, c.species)
         acc, _ = ctx.tree_force(theta, 0.01)
     a_dir = _direct(orc, c.pos, c, tl)

@@ -72,7 +72,8 @@ def test_sort_ties_by_index(U, orc):
 
 
 # ----------------------------------------------------------------- a4-a5
-@pytest.mark.parametrize("leaf_cap", [1, 4, 16])
+# 32: the largest population counted from the window of first depths, 33: searches
+@pytest.mark.parametrize("leaf_cap", [1, 4, 16, 32, 33])
 @pytest.mark.parametrize("n,sigma,seed", [(2048, 1.0, 1), (3000, 1.5, 9)])
 def test_box_table(U, orc, leaf_cap, n, sigma, seed):
     c = gaussian_cloud(n, sigma, seed)
