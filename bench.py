@@ -471,8 +471,11 @@ def run_gpu(args):
             "oracle_tree_force_rel_rms_vs_direct": a0["oracle_tree_vs_direct"]["force"],
             "force_rel_rms_vs_oracle_tree": a0["gpu_vs_oracle_tree"]["force"],
             "theta": W["theta"], "leaf_cap": W["leaf_cap"], "targets": int(tl.size),
+            "particle_steps_per_s": pst,
             "state": "initial state of the workload; FP32C tree forces against the FP64 direct "
-                     "sum on seeded targets (oracle)"}
+                     "sum on seeded targets (oracle)",
+            "note": "particle-steps/s at this force error compares leaf populations; "
+                    "interactions/s counts a direct pair like a multipole"}
         for th, a in accs.items():
             if "theta_sweep" in out and th in out["theta_sweep"]:
                 out["theta_sweep"][th]["accuracy"] = a
