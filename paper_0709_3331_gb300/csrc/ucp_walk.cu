@@ -354,7 +354,12 @@ k_walk_fp32c(WalkArgs a)
             xh = (float)X; yh = (float)Y; zh = (float)Z;
             xl = (float)(X - (double)xh); yl = (float)(Y - (double)yh); zl = (float)(Z - (double)zh);
         }
-        const float2 xyh = make_float2(xh, yh), xyl = make_float2(xl, yl);
+        const float2 xyh = make_float2(xh, yh);
+        // Window of the FP32 criterion (see the traversal): |dm| <= wa d2 + wb
+        // bounds the FP32 error of d2 - rcrit2 for this target, given
+        // |x_t - xh| <= 2^-24 |x_t| and the same for the centroid
+        const float bt = 5e-7f * fmaxf(fabsf(xh), fmaxf(fabsf(yh), fabsf(zh)));
+        const float wa = fmaf(0.5f, bt, 4e-6f), wb = 0.5f * bt;
         const float qt = valid ? (a.sp[t] ? (float)q1 : (float)q0) : 0.f;
         const float inv_lambda = (float)(1.0 / a.lambda);
         const float inv_lambda3 = inv_lambda * inv_lambda * inv_lambda;
@@ -571,17 +576,23 @@ k_walk_fp32c(WalkArgs a)
             const int nxt = __float_as_int(B.w);
             const bool leaf = __float_as_int(C.y) >= 0;
             const bool active = node >= skip;
-            const float2 rxy = __fadd2_rn(__fadd2_rn(xyh, make_float2(A.x, A.y)),
-                                          __fadd2_rn(xyl, make_float2(B.x, B.y)));
+            // R = x_t - c from the rounded target and centroid (their low parts
+            // enter only the direct pairs): one add per axis on the chain
+            // record -> criterion -> vote -> next box that sets the walk's pace
+            const float2 rxy = __fadd2_rn(xyh, make_float2(A.x, A.y));
             const float rx = rxy.x, ry = rxy.y;
-            const float rz = (zh + A.z) + (zl + B.z);
+            const float rz = zh + A.z;
             float d2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
             const float dm = d2 - A.w;
             bool acc = active && dm > 0.f;
-            // Within FP32 rounding of the threshold the decision is taken again in
+            // Within the FP32 error of d2 - rcrit2 the decision is taken again in
             // FP64 exactly as the FP64 walk takes it, so both precisions open the
-            // same boxes (rare: |d2 - rcrit2| <= 4e-6 d2).
-            if (active && fabsf(dm) <= 4e-6f * d2) {
+            // same boxes.  Per axis R is off by at most 2^-23 (|x_t| + |R|), so
+            // |error| <= 2^-22 sqrt(3) X_t d + 2^-21 d2 (rcrit2's rounding
+            // included) with X_t the target's largest coordinate; with
+            // d <= (d2 + 1) / 2 that lies inside wa d2 + wb (rare: a few tests in
+            // a million at the bench size).
+            if (active && fabsf(dm) <= fmaf(wa, d2, wb)) {
                 const double* m = a.t.mom + (size_t)node * kMom;
                 double dx = __dsub_rn(a.x[t], m[0]);
                 double dy = __dsub_rn(a.y[t], m[1]);
