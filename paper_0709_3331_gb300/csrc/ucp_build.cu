@@ -101,6 +101,44 @@ __global__ void k_scan_apply(const int* __restrict__ in, int* __restrict__ out, 
     }
 }
 
+// Target selection: the slots whose species is `species`, in slot order.  The
+// count per tile and the write pass take the flag straight from the species.
+__global__ void k_select_count(const int8_t* __restrict__ sp, int species, int n,
+                               int* __restrict__ part)
+{
+    int base = blockIdx.x * kScanTile;
+    int s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        int i = base + threadIdx.x * kScanItems + k;
+        if (i < n) s += sp[i] == species;
+    }
+    __shared__ int tot;
+    block_excl_scan(s, &tot);
+    if (threadIdx.x == 0) part[blockIdx.x] = tot;
+}
+
+__global__ void k_select_write(const int8_t* __restrict__ sp, int species, int n,
+                               const int* __restrict__ part, int* __restrict__ list)
+{
+    int base = blockIdx.x * kScanTile;
+    int v[kScanItems];
+    int s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        int i = base + threadIdx.x * kScanItems + k;
+        v[k] = i < n && sp[i] == species;
+        s += v[k];
+    }
+    __shared__ int tot;
+    int off = block_excl_scan(s, &tot) + part[blockIdx.x];
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        int i = base + threadIdx.x * kScanItems + k;
+        if (v[k]) list[off++] = i;
+    }
+}
+
 // ---------------------------------------------------------------- cube
 // Ordered integer image of a finite double: comparing the images compares the
 // values, so min/max run on the integer ALU instead of the (scarce) FP64 pipe.
@@ -206,13 +244,15 @@ __device__ __forceinline__ unsigned long long spread3(unsigned int v)
     return x;
 }
 
-// cell coordinate k = floor((x - lo) * (2^21 / L)), clamped to [0, 2^21 - 1]
+// cell coordinate k = floor((x - lo) * (2^21 / L)), clamped to [0, 2^21 - 1].
+// Truncation toward zero equals floor wherever the clamp keeps the value (it
+// differs only below 0, which clamps to 0 either way), and the saturating
+// conversion keeps values past the int range above the upper clamp: three FP64
+// operations per axis, the clamps on the integer ALU.
 __device__ __forceinline__ unsigned int cell_coord(double x, double lo, double kscale)
 {
-    double u = floor(__dmul_rn(__dsub_rn(x, lo), kscale));
-    if (!(u > 0.0)) return 0u;
-    if (u >= 2097151.0) return 2097151u;
-    return (unsigned int)u;
+    const int k = __double2int_rz(__dmul_rn(__dsub_rn(x, lo), kscale));
+    return (unsigned int)min(max(k, 0), 2097151);
 }
 
 __global__ void k_keys(const double* __restrict__ x, const double* __restrict__ y,
@@ -1052,6 +1092,24 @@ void launch_scan(const int* in, int* out, int n, int* partials, int* total, cuda
     k_scan_reduce<<<nb, kScanThreads, 0, s>>>(in, n, partials);
     k_scan_partials<<<1, kScanThreads, 0, s>>>(partials, nb, total);
     k_scan_apply<<<nb, kScanThreads, 0, s>>>(in, out, n, partials);
+}
+
+void launch_select(const int8_t* sp, int species, int n, int* list, int* partials, int* count,
+                   cudaStream_t s)
+{
+    count_launch(3);
+    int nb = (n + kScanTile - 1) / kScanTile;
+    if (nb < 1) nb = 1;
+    k_select_count<<<nb, kScanThreads, 0, s>>>(sp, species, n, partials);
+    k_scan_partials<<<1, kScanThreads, 0, s>>>(partials, nb, count);
+    k_select_write<<<nb, kScanThreads, 0, s>>>(sp, species, n, partials, list);
+}
+
+void launch_bbox_final(const double* partials, int nblk, Cube* cubes, int n_clouds,
+                       cudaStream_t s)
+{
+    count_launch(1);
+    k_bbox_final<<<n_clouds, 256, 0, s>>>(partials, nblk, cubes);
 }
 
 void launch_bbox(const double* x, const double* y, const double* z, int n, double* partials,

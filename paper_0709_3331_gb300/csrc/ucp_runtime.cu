@@ -46,10 +46,11 @@ struct ucp_ctx {
     Cube* cube = nullptr;
     double* bbox_part = nullptr;
     int bbox_nblk = 1;
+    int kd_nblk = 0;         // bounding-box partials left by the kick-drift (one cloud)
+    bool bbox_ready = false; // those partials describe the current positions
     double* qsp = nullptr;
     double* msp = nullptr;
-    int* tflags = nullptr;
-    int* tlist = nullptr;    // 2n: compacted list, then scan offsets
+    int* tlist = nullptr;    // selected targets (electrons), key order
     int* tcount = nullptr;
     int* cnt_p2p = nullptr;
     int* cnt_m2p = nullptr;
@@ -208,8 +209,12 @@ int build(ucp_ctx* c)
 {
     int n = c->n, k = c->cur;
     const int* cs = c->n_clouds > 1 ? c->cloud_start : nullptr;
-    launch_bbox(c->st[k][0], c->st[k][1], c->st[k][2], n, c->bbox_part, c->bbox_nblk, c->cube,
-                cs, c->n_clouds, c->s);
+    if (c->bbox_ready)  // partials of the positions left by the kick-drift
+        launch_bbox_final(c->bbox_part, c->kd_nblk, c->cube, 1, c->s);
+    else
+        launch_bbox(c->st[k][0], c->st[k][1], c->st[k][2], n, c->bbox_part, c->bbox_nblk, c->cube,
+                    cs, c->n_clouds, c->s);
+    c->bbox_ready = false;
     launch_keys(c->st[k][0], c->st[k][1], c->st[k][2], n, c->cube, c->t.cloud, c->key[0],
                 c->val[0], c->s);
     const int b = launch_sort(c->key, c->val, n, c->sort, c->id[k], c->t.cloud, c->cloud_start,
@@ -249,8 +254,7 @@ int force(ucp_ctx* c, double theta, double eps, int electrons_only, bool want_ph
     a.src32 = c->src32;
     a.t = c->t;
     if (electrons_only) {
-        launch_select(c->sp[k], UCP_ELECTRON, c->n, c->tflags, c->tlist, c->scan_part, c->tcount,
-                      c->s);
+        launch_select(c->sp[k], UCP_ELECTRON, c->n, c->tlist, c->scan_part, c->tcount, c->s);
         a.targets = c->tlist;
         a.ntargets = c->n_e;
         a.chunks = c->chunks_e;
@@ -526,7 +530,9 @@ int ucp_create_batch(ucp_ctx** out, const ucp_params* p, int32_t n_clouds, const
     c->en_nblk = (int)((n + 2047) / 2048);
     if (c->en_nblk > 4 * c->nsm) c->en_nblk = 4 * c->nsm;
     if (c->en_nblk < 1) c->en_nblk = 1;
-    if ((rc = dalloc(c, &c->bbox_part, (size_t)n_clouds * c->bbox_nblk * 6)) ||
+    c->kd_nblk = n_clouds == 1 ? kick_drift_blocks((int)n) : 0;
+    if ((rc = dalloc(c, &c->bbox_part,
+                     (size_t)6 * std::max((int64_t)n_clouds * c->bbox_nblk, (int64_t)c->kd_nblk))) ||
         (rc = dalloc(c, &c->en_part, (size_t)c->en_nblk * 6)) ||
         (rc = dalloc(c, &c->en_out, (size_t)6 * n_clouds)))
         return bail(rc);
@@ -559,8 +565,7 @@ int ucp_create_batch(ucp_ctx** out, const ucp_params* p, int32_t n_clouds, const
             return bail(rc);
     }
     if ((rc = dalloc(c, &c->qsp, 2)) || (rc = dalloc(c, &c->msp, 2))) return bail(rc);
-    if ((rc = dalloc(c, &c->tflags, n)) || (rc = dalloc(c, &c->tlist, 2 * n)) ||
-        (rc = dalloc(c, &c->tcount, 1)))
+    if ((rc = dalloc(c, &c->tlist, n)) || (rc = dalloc(c, &c->tcount, 1)))
         return bail(rc);
     if ((rc = dalloc(c, &c->cnt_p2p, n)) || (rc = dalloc(c, &c->cnt_m2p, n)) ||
         (rc = dalloc(c, &c->work, 1)) || (rc = dalloc(c, &c->stats, 2)) ||
@@ -643,6 +648,7 @@ int ucp_set_state(ucp_ctx* c, const double* pos, const double* vel, const int8_t
     c->tree_valid = false;
     c->acc_valid = false;
     c->phi_valid = false;
+    c->bbox_ready = false;
     c->steps = 0;
     int rc = check_launch(c, "set_state");
     if (rc) return rc;
@@ -727,17 +733,18 @@ static int run_blocks(ucp_ctx* c, double dt_e, int kk, int64_t nblocks, double t
     const double h_i = 0.5 * dt_i, h_e = 0.5 * dt_e;
     int pend_i = 0, pend_e = 0;
     for (int64_t b = 0; b < nblocks; ++b) {
-        int k = c->cur;
-        launch_kick(c->st[k][3], c->st[k][4], c->st[k][5], c->ax, c->ay, c->az, c->sp[k], UCP_ION,
-                    h_i, c->n, 1 + pend_i, c->s);
-        pend_i = 0;
         for (int sub = 1; sub <= kk; ++sub) {
-            k = c->cur;
-            launch_kick(c->st[k][3], c->st[k][4], c->st[k][5], c->ax, c->ay, c->az, c->sp[k],
-                        UCP_ELECTRON, h_e, c->n, 1 + pend_e, c->s);
+            // the electrons' kicks (with the one left from the last substep), the
+            // ions' at the start of a block, then the drift, in one pass; a
+            // single cloud's bounding-box partials come with it
+            int k = c->cur;
+            const int ti = sub == 1 ? 1 + pend_i : 0;
+            double* part = c->n_clouds == 1 ? c->bbox_part : nullptr;
+            launch_kick_drift(c->st[k], c->ax, c->ay, c->az, c->sp[k], h_e, 1 + pend_e, h_i, ti,
+                              dt_e, c->n, part, c->s);
+            c->bbox_ready = part != nullptr;
             pend_e = 0;
-            launch_drift(c->st[k][0], c->st[k][1], c->st[k][2], c->st[k][3], c->st[k][4],
-                         c->st[k][5], dt_e, c->n, c->s);
+            if (sub == 1) pend_i = 0;
             if ((rc = build(c))) return rc;
             // the walk over every particle also leaves phi for a following ucp_energy
             if ((rc = force(c, theta, eps, sub < kk, sub == kk))) return rc;
@@ -992,6 +999,7 @@ static void load_state(ucp_ctx* c, const double* dpos, const double* dvel)
     c->tree_valid = false;
     c->acc_valid = false;
     c->phi_valid = false;
+    c->bbox_ready = false;
 }
 
 int ucp_grad_ke_electrons(ucp_ctx* c, double dt_e, int kk, int64_t n_steps, double theta,
@@ -1083,7 +1091,7 @@ int ucp_grad_ke_electrons(ucp_ctx* c, double dt_e, int kk, int64_t n_steps, doub
             if (ci == 0.0 && c->n_e > 0) {
                 // inside a block the ions' weights are zero: only the electrons'
                 // accelerations carry adjoint weight, so only they are walked
-                launch_select(c->sp[k], UCP_ELECTRON, c->n, c->tflags, c->tlist, c->scan_part,
+                launch_select(c->sp[k], UCP_ELECTRON, c->n, c->tlist, c->scan_part,
                               c->tcount, c->s);
                 a.targets = c->tlist;
                 a.ntargets = c->n_e;
