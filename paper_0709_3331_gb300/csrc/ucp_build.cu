@@ -1105,13 +1105,6 @@ void launch_select(const int8_t* sp, int species, int n, int* list, int* partial
     k_select_write<<<nb, kScanThreads, 0, s>>>(sp, species, n, partials, list);
 }
 
-void launch_bbox_final(const double* partials, int nblk, Cube* cubes, int n_clouds,
-                       cudaStream_t s)
-{
-    count_launch(1);
-    k_bbox_final<<<n_clouds, 256, 0, s>>>(partials, nblk, cubes);
-}
-
 void launch_bbox(const double* x, const double* y, const double* z, int n, double* partials,
                  int nblk, Cube* cubes, const int* cloud_start, int n_clouds, cudaStream_t s)
 {

@@ -88,9 +88,6 @@ struct Cube {                // enclosing cube: centre, side, lower corner, 2^21
 // ---- build (ucp_build.cu) ----
 void launch_bbox(const double* x, const double* y, const double* z, int n, double* partials,
                  int nblk, Cube* cubes, const int* cloud_start, int n_clouds, cudaStream_t s);
-// the cube(s) from nblk partials per cloud already in place
-void launch_bbox_final(const double* partials, int nblk, Cube* cubes, int n_clouds,
-                       cudaStream_t s);
 void launch_keys(const double* x, const double* y, const double* z, int n, const Cube* cubes,
                  const unsigned char* cloud, unsigned long long* key, unsigned int* val,
                  cudaStream_t s);
@@ -178,13 +175,8 @@ void launch_kick(double* vx, double* vy, double* vz, const double* ax, const dou
 // partials holds scan_partials_words(n) ints
 void launch_select(const int8_t* sp, int species, int n, int* list, int* partials, int* count,
                    cudaStream_t s);
-// The kicks and drift of one substep in one pass over the state st = {x, y, z,
-// vx, vy, vz}; with part != NULL (single-cloud contexts) it also leaves
-// kick_drift_blocks(n) bounding-box partials for launch_bbox_final.
-int kick_drift_blocks(int n);
-void launch_kick_drift(double* const* st, const double* ax, const double* ay, const double* az,
-                       const int8_t* sp, double he, int te, double hi, int ti, double dt, int n,
-                       double* part, cudaStream_t s);
+void launch_drift(double* x, double* y, double* z, const double* vx, const double* vy,
+                  const double* vz, double dt, int n, cudaStream_t s);
 void launch_energy(const double* vx, const double* vy, const double* vz, const double* phi,
                    const int8_t* sp, const double* qsp, const double* msp, int n,
                    double* partials, int nblk, double* out6, cudaStream_t s);

@@ -55,80 +55,15 @@ __global__ void k_kick(double* __restrict__ vx, double* __restrict__ vy, double*
     vz[i] = uz;
 }
 
-// One substep of the split step: the velocity kicks k_kick would apply (ions ti
-// times by hi, electrons te times by he, each rounded on its own), then the
-// drift of every particle by dt, kKdItems particles per thread.  With part !=
-// NULL each block also leaves the min and max of its drifted positions (as
-// k_bbox_partial does) for the root cube of the build that follows.
-constexpr int kKdItems = 4;
-
-__global__ void __launch_bounds__(kT)
-k_kick_drift(double* __restrict__ x, double* __restrict__ y, double* __restrict__ z,
-             double* __restrict__ vx, double* __restrict__ vy, double* __restrict__ vz,
-             const double* __restrict__ ax, const double* __restrict__ ay,
-             const double* __restrict__ az, const int8_t* __restrict__ sp, double he, int te,
-             double hi, int ti, double dt, int n, double* __restrict__ part)
+__global__ void k_drift(double* __restrict__ x, double* __restrict__ y, double* __restrict__ z,
+                        const double* __restrict__ vx, const double* __restrict__ vy,
+                        const double* __restrict__ vz, double dt, int n)
 {
-    unsigned long long lo[3] = {~0ull, ~0ull, ~0ull}, hi3[3] = {0ull, 0ull, 0ull};
-#pragma unroll
-    for (int it = 0; it < kKdItems; ++it) {
-        const int i = (blockIdx.x * kKdItems + it) * kT + threadIdx.x;
-        if (i >= n) break;
-        const bool e = sp[i] != 0;
-        const double h = e ? he : hi;
-        const int times = e ? te : ti;
-        double ux = vx[i], uy = vy[i], uz = vz[i];
-        if (times > 0) {
-            const double gx = ax[i], gy = ay[i], gz = az[i];
-            for (int k = 0; k < times; ++k) {  // as k_kick
-                ux = __fma_rn(h, gx, ux);
-                uy = __fma_rn(h, gy, uy);
-                uz = __fma_rn(h, gz, uz);
-            }
-            vx[i] = ux;
-            vy[i] = uy;
-            vz[i] = uz;
-        }
-        const double X = __fma_rn(dt, ux, x[i]), Y = __fma_rn(dt, uy, y[i]),
-                     Z = __fma_rn(dt, uz, z[i]);
-        x[i] = X;
-        y[i] = Y;
-        z[i] = Z;
-        const unsigned long long o[3] = {ord64(X), ord64(Y), ord64(Z)};
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            lo[a] = min(lo[a], o[a]);
-            hi3[a] = max(hi3[a], o[a]);
-        }
-    }
-    if (!part) return;
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            lo[a] = min(lo[a], __shfl_xor_sync(0xffffffffu, lo[a], o));
-            hi3[a] = max(hi3[a], __shfl_xor_sync(0xffffffffu, hi3[a], o));
-        }
-    __shared__ unsigned long long sh[kT / 32][6];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    if (lane == 0)
-        for (int a = 0; a < 3; ++a) {
-            sh[w][a] = lo[a];
-            sh[w][3 + a] = hi3[a];
-        }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        for (int ww = 1; ww < kT / 32; ++ww)
-            for (int a = 0; a < 3; ++a) {
-                sh[0][a] = min(sh[0][a], sh[ww][a]);
-                sh[0][3 + a] = max(sh[0][3 + a], sh[ww][3 + a]);
-            }
-        double* pp = part + (size_t)blockIdx.x * 6;
-        for (int a = 0; a < 3; ++a) {
-            pp[a] = sh[0][a] == ~0ull ? INFINITY : unord64(sh[0][a]);
-            pp[3 + a] = sh[0][3 + a] == 0ull ? -INFINITY : unord64(sh[0][3 + a]);
-        }
-    }
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    x[i] = __fma_rn(dt, vx[i], x[i]);  // one rounding, as the kicks
+    y[i] = __fma_rn(dt, vy[i], y[i]);
+    z[i] = __fma_rn(dt, vz[i], z[i]);
 }
 
 // Deterministic two-level reduction: fixed per-thread strides, fixed tree in
@@ -285,19 +220,11 @@ void launch_kick(double* vx, double* vy, double* vz, const double* ax, const dou
     k_kick<<<nb(n), kT, 0, s>>>(vx, vy, vz, ax, ay, az, sp, species, h, n, times);
 }
 
-int kick_drift_blocks(int n)
-{
-    const int b = (n + kT * kKdItems - 1) / (kT * kKdItems);
-    return b < 1 ? 1 : b;
-}
-
-void launch_kick_drift(double* const* st, const double* ax, const double* ay, const double* az,
-                       const int8_t* sp, double he, int te, double hi, int ti, double dt, int n,
-                       double* part, cudaStream_t s)
+void launch_drift(double* x, double* y, double* z, const double* vx, const double* vy,
+                  const double* vz, double dt, int n, cudaStream_t s)
 {
     count_launch(1);
-    k_kick_drift<<<kick_drift_blocks(n), kT, 0, s>>>(st[0], st[1], st[2], st[3], st[4], st[5], ax,
-                                                     ay, az, sp, he, te, hi, ti, dt, n, part);
+    k_drift<<<nb(n), kT, 0, s>>>(x, y, z, vx, vy, vz, dt, n);
 }
 
 void launch_energy(const double* vx, const double* vy, const double* vz, const double* phi,

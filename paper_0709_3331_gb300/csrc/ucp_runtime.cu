@@ -46,8 +46,6 @@ struct ucp_ctx {
     Cube* cube = nullptr;
     double* bbox_part = nullptr;
     int bbox_nblk = 1;
-    int kd_nblk = 0;         // bounding-box partials left by the kick-drift (one cloud)
-    bool bbox_ready = false; // those partials describe the current positions
     double* qsp = nullptr;
     double* msp = nullptr;
     int* tlist = nullptr;    // selected targets (electrons), key order
@@ -209,12 +207,8 @@ int build(ucp_ctx* c)
 {
     int n = c->n, k = c->cur;
     const int* cs = c->n_clouds > 1 ? c->cloud_start : nullptr;
-    if (c->bbox_ready)  // partials of the positions left by the kick-drift
-        launch_bbox_final(c->bbox_part, c->kd_nblk, c->cube, 1, c->s);
-    else
-        launch_bbox(c->st[k][0], c->st[k][1], c->st[k][2], n, c->bbox_part, c->bbox_nblk, c->cube,
-                    cs, c->n_clouds, c->s);
-    c->bbox_ready = false;
+    launch_bbox(c->st[k][0], c->st[k][1], c->st[k][2], n, c->bbox_part, c->bbox_nblk, c->cube,
+                cs, c->n_clouds, c->s);
     launch_keys(c->st[k][0], c->st[k][1], c->st[k][2], n, c->cube, c->t.cloud, c->key[0],
                 c->val[0], c->s);
     const int b = launch_sort(c->key, c->val, n, c->sort, c->id[k], c->t.cloud, c->cloud_start,
@@ -530,9 +524,7 @@ int ucp_create_batch(ucp_ctx** out, const ucp_params* p, int32_t n_clouds, const
     c->en_nblk = (int)((n + 2047) / 2048);
     if (c->en_nblk > 4 * c->nsm) c->en_nblk = 4 * c->nsm;
     if (c->en_nblk < 1) c->en_nblk = 1;
-    c->kd_nblk = n_clouds == 1 ? kick_drift_blocks((int)n) : 0;
-    if ((rc = dalloc(c, &c->bbox_part,
-                     (size_t)6 * std::max((int64_t)n_clouds * c->bbox_nblk, (int64_t)c->kd_nblk))) ||
+    if ((rc = dalloc(c, &c->bbox_part, (size_t)n_clouds * c->bbox_nblk * 6)) ||
         (rc = dalloc(c, &c->en_part, (size_t)c->en_nblk * 6)) ||
         (rc = dalloc(c, &c->en_out, (size_t)6 * n_clouds)))
         return bail(rc);
@@ -648,7 +640,6 @@ int ucp_set_state(ucp_ctx* c, const double* pos, const double* vel, const int8_t
     c->tree_valid = false;
     c->acc_valid = false;
     c->phi_valid = false;
-    c->bbox_ready = false;
     c->steps = 0;
     int rc = check_launch(c, "set_state");
     if (rc) return rc;
@@ -733,18 +724,17 @@ static int run_blocks(ucp_ctx* c, double dt_e, int kk, int64_t nblocks, double t
     const double h_i = 0.5 * dt_i, h_e = 0.5 * dt_e;
     int pend_i = 0, pend_e = 0;
     for (int64_t b = 0; b < nblocks; ++b) {
+        int k = c->cur;
+        launch_kick(c->st[k][3], c->st[k][4], c->st[k][5], c->ax, c->ay, c->az, c->sp[k], UCP_ION,
+                    h_i, c->n, 1 + pend_i, c->s);
+        pend_i = 0;
         for (int sub = 1; sub <= kk; ++sub) {
-            // the electrons' kicks (with the one left from the last substep), the
-            // ions' at the start of a block, then the drift, in one pass; a
-            // single cloud's bounding-box partials come with it
-            int k = c->cur;
-            const int ti = sub == 1 ? 1 + pend_i : 0;
-            double* part = c->n_clouds == 1 ? c->bbox_part : nullptr;
-            launch_kick_drift(c->st[k], c->ax, c->ay, c->az, c->sp[k], h_e, 1 + pend_e, h_i, ti,
-                              dt_e, c->n, part, c->s);
-            c->bbox_ready = part != nullptr;
+            k = c->cur;
+            launch_kick(c->st[k][3], c->st[k][4], c->st[k][5], c->ax, c->ay, c->az, c->sp[k],
+                        UCP_ELECTRON, h_e, c->n, 1 + pend_e, c->s);
             pend_e = 0;
-            if (sub == 1) pend_i = 0;
+            launch_drift(c->st[k][0], c->st[k][1], c->st[k][2], c->st[k][3], c->st[k][4],
+                         c->st[k][5], dt_e, c->n, c->s);
             if ((rc = build(c))) return rc;
             // the walk over every particle also leaves phi for a following ucp_energy
             if ((rc = force(c, theta, eps, sub < kk, sub == kk))) return rc;
@@ -999,7 +989,6 @@ static void load_state(ucp_ctx* c, const double* dpos, const double* dvel)
     c->tree_valid = false;
     c->acc_valid = false;
     c->phi_valid = false;
-    c->bbox_ready = false;
 }
 
 int ucp_grad_ke_electrons(ucp_ctx* c, double dt_e, int kk, int64_t n_steps, double theta,
