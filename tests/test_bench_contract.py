@@ -27,3 +27,29 @@ def test_reference_arm_json_line(capsys, monkeypatch):
     assert d["metric"] == bench.METRIC and d["config"]["workload"] == bench.WORKLOAD["name"]
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
+
+
+def test_traffic_record_is_gated(monkeypatch):
+    """The roofline's DRAM traffic comes from the committed ncu record only while
+    the walk source and the leaf population are those of the capture; it is the
+    block's launch mix (one full walk, k - 1 electron walks)."""
+    sys.path.insert(0, ROOT)
+    import hashlib
+    import bench
+    rec = {}
+    for line in open(os.path.join(ROOT, "profiles", "walk_fp32c_traffic.txt")):
+        if ":" in line:
+            k, v = line.split(":", 1)
+            rec[k.strip()] = v.strip()
+    src = os.path.join(ROOT, "paper_0709_3331_gb300", "csrc", "ucp_walk.cu")
+    same = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] == rec["walk_source_sha256_16"]
+    got = bench.traffic_record()
+    if same and rec.get("leaf_cap") == str(bench.WORKLOAD["leaf_cap"]):
+        k = bench.WORKLOAD["k"]
+        want = (float(rec["dram_bytes_per_full_walk"]) +
+                (k - 1) * float(rec["dram_bytes_per_electron_walk"])) / k
+        assert got == want
+    else:
+        assert got is None
+    monkeypatch.setitem(bench.WORKLOAD, "leaf_cap", bench.WORKLOAD["leaf_cap"] + 1)
+    assert bench.traffic_record() is None
