@@ -294,34 +294,30 @@ __device__ __forceinline__ void qmulf(const float* Q, const float* v, float* o)
     o[2] = fmaf(Q[2], v[0], fmaf(Q[4], v[1], Q[5] * v[2]));
 }
 
-// The fourth-derivative term of the expansion contracted with two vectors v1, v2
-// (one tensor, shared parts formed once):
+// The fourth-derivative term of the expansion contracted with a vector v:
 //   o_a = 105 R_a (R.v)(R.Q.R) g^9 - 15 g^7 (v_a R.Q.R + 2 (R.v)(QR)_a + 2 R_a v.QR
 //         + R_a (R.v) tr Q) + 3 g^5 (v_a tr Q + 2 (Qv)_a),
-// collected as coefficients of R_a, (QR)_a, v_a and (Qv)_a.
-__device__ __forceinline__ void t4f2(const float* R, const float* v1, const float* v2,
-                                     const float* Q, float g5, float g7, float g9, float Rv1,
-                                     float Rv2, float* o1, float* o2)
+// collected as coefficients of R_a, (QR)_a, v_a and (Qv)_a.  It is linear in v:
+// the source side's weight w = (q/m) lambda takes it as q/m times lambda's.
+__device__ __forceinline__ void t4f(const float* R, const float* v, const float* Q, float g5,
+                                    float g7, float g9, float Rv, float* o)
 {
-    float QR[3];
+    float QR[3], Qv[3];
     qmulf(Q, R, QR);
+    qmulf(Q, v, Qv);
     const float RQR = dot3f(R, QR), trQ = Q[0] + Q[3] + Q[5];
     const float cv = 3.f * g5 * trQ - 15.f * g7 * RQR;
     const float cqv = 6.f * g5;
-    auto one = [&](const float* v, float Rv, float* o) {
-        float Qv[3];
-        qmulf(Q, v, Qv);
-        const float vQR = dot3f(v, QR);
-        const float cr = 105.f * Rv * RQR * g9 - 15.f * g7 * (2.f * vQR + Rv * trQ);
-        const float cq = -30.f * g7 * Rv;
+    const float vQR = dot3f(v, QR);
+    const float cr = 105.f * Rv * RQR * g9 - 15.f * g7 * (2.f * vQR + Rv * trQ);
+    const float cq = -30.f * g7 * Rv;
 #pragma unroll
-        for (int a = 0; a < 3; ++a) o[a] = fmaf(cr, R[a], fmaf(cq, QR[a], fmaf(cv, v[a], cqv * Qv[a])));
-    };
-    one(v1, Rv1, o1);
-    one(v2, Rv2, o2);
+    for (int a = 0; a < 3; ++a) o[a] = fmaf(cr, R[a], fmaf(cq, QR[a], fmaf(cv, v[a], cqv * Qv[a])));
 }
 
-__global__ void __launch_bounds__(kAdjThreads)
+// 8 blocks of 128 per SM (64 registers): more resident warps for this issue-bound
+// walk than the compiler's own choice, without spills
+__global__ void __launch_bounds__(kAdjThreads, 8)
 k_walk_adjoint_f32(WalkArgs a, const double* __restrict__ lam, double* __restrict__ mu,
                    float* __restrict__ adj)
 {
@@ -355,7 +351,8 @@ k_walk_adjoint_f32(WalkArgs a, const double* __restrict__ lam, double* __restric
             const int s = a.sp[t];
             qm = (float)((s ? q1 : q0) / a.msp[s]);
         }
-        const float wv[3] = {qm * l[0], qm * l[1], qm * l[2]};
+        // the source side's weight is w = (q/m) lambda: every source-side term is
+        // q/m times the target side's form in lambda
         float mt[3] = {0.f, 0.f, 0.f};
         int skip = valid ? 0 : 0x7fffffff;
         int npl = 0;
@@ -380,14 +377,18 @@ k_walk_adjoint_f32(WalkArgs a, const double* __restrict__ lam, double* __restric
                                        rz + (odd ? Q.y : Q.x)};
                         float g = rsqrt_ftz(dot3f(r3, r3) + eps2);
                         float g3 = g * g * g, g5 = g3 * g * g;
-                        float rl = dot3f(r3, l), rw = dot3f(r3, wv);
+                        const float rl = dot3f(r3, l), qq = qm * qj;
+                        // the pair's term on the target; the source takes its negative
+                        const float cl = qq * g3, cr = -3.f * qq * rl * g5;
+                        float tv[3];
 #pragma unroll
                         for (int c = 0; c < 3; ++c) {
-                            mt[c] = fmaf(qm * qj, l[c] * g3 - 3.f * r3[c] * rl * g5, mt[c]);
+                            tv[c] = fmaf(cl, l[c], cr * r3[c]);
+                            mt[c] += tv[c];
                         }
-                        sx = -qj * (wv[0] * g3 - 3.f * r3[0] * rw * g5);
-                        sy = -qj * (wv[1] * g3 - 3.f * r3[1] * rw * g5);
-                        sz = -qj * (wv[2] * g3 - 3.f * r3[2] * rw * g5);
+                        sx = -tv[0];
+                        sy = -tv[1];
+                        sz = -tv[2];
                     }
                     float sv[4] = {sx, sy, sz, 0.f};
                     const float tot = warp_sum4(sv, lane);
@@ -446,9 +447,8 @@ k_walk_adjoint_f32(WalkArgs a, const double* __restrict__ lam, double* __restric
                     const float g = rsqrt_ftz(d2 + eps2);
                     const float g2 = g * g, g3 = g2 * g, g5 = g3 * g2, g7 = g5 * g2, g9 = g7 * g2;
                     const float Rl = dot3f(R, l), RD = dot3f(R, D), lD = dot3f(l, D);
-                    const float Rw = dot3f(R, wv);
-                    float T4l[3], T4w[3];
-                    t4f2(R, l, wv, Q, g5, g7, g9, Rl, Rw, T4l, T4w);
+                    float T4l[3];
+                    t4f(R, l, Q, g5, g7, g9, Rl, T4l);
                     // monopole Hessian M (3 R (R.l) g^5 - l g^3) minus the dipole term
                     // -15 R (R.l)(R.D) g^7 + 3 (l (R.D) + D (R.l) + R (l.D)) g^5,
                     // collected as coefficients of R, l and D
@@ -458,17 +458,20 @@ k_walk_adjoint_f32(WalkArgs a, const double* __restrict__ lam, double* __restric
 #pragma unroll
                     for (int c = 0; c < 3; ++c)
                         mt[c] -= qm * fmaf(aR, R[c], fmaf(al, l[c], fmaf(aD, D[c], 0.5f * T4l[c])));
+                    // source side in w = (q/m) lambda: q/m times the lambda forms
+                    const float Rw = qm * Rl, w5 = 3.f * qm * g5, w3 = qm * g3, hq = 0.5f * qm;
 #pragma unroll
                     for (int c = 0; c < 3; ++c) {
-                        src[c] = 3.f * R[c] * Rw * g5 - wv[c] * g3;
-                        src[9 + c] = 0.5f * T4w[c];
+                        src[c] = fmaf(3.f * Rw * g5, R[c], -w3 * l[c]);
+                        src[9 + c] = hq * T4l[c];
                     }
                     const int ia[6] = {0, 0, 0, 1, 1, 2}, ib[6] = {0, 1, 2, 1, 2, 2};
+                    const float r7 = -15.f * Rw * g7;
 #pragma unroll
                     for (int k = 0; k < 6; ++k) {
                         const int e = ia[k], c = ib[k];
-                        src[3 + k] = -15.f * Rw * R[e] * R[c] * g7 +
-                                     3.f * (wv[e] * R[c] + wv[c] * R[e] + (e == c ? Rw : 0.f)) * g5;
+                        src[3 + k] = fmaf(r7 * R[e], R[c],
+                                          w5 * (l[e] * R[c] + l[c] * R[e] + (e == c ? Rl : 0.f)));
                     }
                 }
                 float sv[16];
