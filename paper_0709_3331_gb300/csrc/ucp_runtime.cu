@@ -1031,11 +1031,16 @@ int ucp_grad_ke_electrons(ucp_ctx* c, double dt_e, int kk, int64_t n_steps, doub
     };
     const double h_e = 0.5 * dt_e, h_i = 0.5 * (double)kk * dt_e;
     int64_t steps0 = c->steps;
-    // forward, checkpoints at g = 0, C, 2C, ...
+    // forward, checkpoints at g = 0, C, 2C, ...; the last segment's positions are
+    // kept as the reverse sweep's first segment (no recomputation of it)
     snapshot(ck);
     for (int64_t sgi = 0; sgi < nseg; ++sgi) {
         int64_t len = std::min(C, S - sgi * C);
-        if ((rc = run_blocks(c, dt_e, kk, len / kk, theta, eps, nullptr))) break;
+        const bool last = sgi == nseg - 1;
+        if (last)
+            cudaMemcpyAsync(seg, ck + 2 * n3 * sgi, sizeof(double) * n3, cudaMemcpyDeviceToDevice,
+                            c->s);
+        if ((rc = run_blocks(c, dt_e, kk, len / kk, theta, eps, last ? seg + n3 : nullptr))) break;
         snapshot(ck + 2 * n3 * (sgi + 1));
     }
     if (rc) {
@@ -1050,11 +1055,13 @@ int ucp_grad_ke_electrons(ucp_ctx* c, double dt_e, int kk, int64_t n_steps, doub
     // reverse: for g = S .. 1: adjoint of the kicks at X_g, then of drift g; X_0 last
     for (int64_t sgi = nseg - 1; sgi >= 0 && !rc; --sgi) {
         const int64_t g0 = sgi * C, len = std::min(C, S - g0);
-        load_state(c, ck + 2 * n3 * sgi, ck + 2 * n3 * sgi + n3);
-        // seg[0] = X_{g0}; seg[j] = X_{g0 + j}
-        cudaMemcpyAsync(seg, ck + 2 * n3 * sgi, sizeof(double) * n3, cudaMemcpyDeviceToDevice,
-                        c->s);
-        if ((rc = run_blocks(c, dt_e, kk, len / kk, theta, eps, seg + n3))) break;
+        // seg[0] = X_{g0}; seg[j] = X_{g0 + j} (the last segment's from the forward run)
+        if (sgi < nseg - 1) {
+            load_state(c, ck + 2 * n3 * sgi, ck + 2 * n3 * sgi + n3);
+            cudaMemcpyAsync(seg, ck + 2 * n3 * sgi, sizeof(double) * n3, cudaMemcpyDeviceToDevice,
+                            c->s);
+            if ((rc = run_blocks(c, dt_e, kk, len / kk, theta, eps, seg + n3))) break;
+        }
         for (int64_t j = len; j >= (sgi == 0 ? 0 : 1); --j) {
             const int64_t g = g0 + j;
             // merged kicks that use a(X_g): electrons 2 h_e (1 at the ends), ions 2 h_i at
