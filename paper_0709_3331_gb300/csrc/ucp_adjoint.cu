@@ -342,7 +342,9 @@ k_walk_adjoint_f32(WalkArgs a, const double* __restrict__ lam, double* __restric
         float l[3] = {0.f, 0.f, 0.f};
         float qm = 0.f;
         if (valid) {
-            double X = a.x[t], Y = a.y[t], Z = a.z[t];
+            // relative to the centre of the cloud's cube, as the box records are
+            const double* cc = a.cubes[ck.z].c;
+            double X = a.x[t] - cc[0], Y = a.y[t] - cc[1], Z = a.z[t] - cc[2];
             xh = (float)X; yh = (float)Y; zh = (float)Z;
             xl = (float)(X - (double)xh); yl = (float)(Y - (double)yh); zl = (float)(Z - (double)zh);
             l[0] = (float)lam[3 * (size_t)t];

@@ -132,6 +132,7 @@ struct WalkArgs {
     const int4* chunks;     // {first target index, count <= 32, cloud, 0}, one cloud each
     int nchunks;
     const int* pos_off;     // first box started at each sorted position (the roots)
+    const Cube* cubes;      // per cloud: FP32C coordinates are taken relative to the centre
     double eps2;
     int kelbg;              // electron-ion pairs use the Kelbg form (Sec. 2.1 Eq. 3)
     double lambda;          // its fixed lambda_ei

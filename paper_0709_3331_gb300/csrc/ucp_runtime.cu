@@ -260,6 +260,7 @@ int force(ucp_ctx* c, double theta, double eps, int electrons_only, bool want_ph
         a.nchunks = c->n_chunks_all;
     }
     a.pos_off = c->pos_off;
+    a.cubes = c->cube;
     a.eps2 = eps * eps;
     a.kelbg = c->potential == UCP_POT_KELBG;
     a.lambda = c->lambda_ei;
@@ -1100,6 +1101,7 @@ int ucp_grad_ke_electrons(ucp_ctx* c, double dt_e, int kk, int64_t n_steps, doub
                 a.nchunks = c->n_chunks_all;
             }
             a.pos_off = c->pos_off;
+            a.cubes = c->cube;
             a.eps2 = eps * eps;
             a.kelbg = 0;
             a.lambda = 1.0;
@@ -1181,6 +1183,7 @@ int ucp_accel_vjp(ucp_ctx* c, double theta, double eps, const double* lam_in, do
     a.chunks = c->chunks_all;
     a.nchunks = c->n_chunks_all;
     a.pos_off = c->pos_off;
+    a.cubes = c->cube;
     a.eps2 = eps * eps;
     a.kelbg = 0;
     a.lambda = 1.0;

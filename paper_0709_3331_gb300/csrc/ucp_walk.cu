@@ -347,10 +347,13 @@ k_walk_fp32c(WalkArgs a)
         const int root = a.pos_off[a.t.cloud_start ? a.t.cloud_start[ck.z] : 0];
         const int end = __float_as_int(F[(size_t)root * kF32 + 1].w);
         // target as an unevaluated float pair: x = xh + xl ({x, y} packed for the
-        // FP32x2 adds)
+        // FP32x2 adds), relative to the centre of the cloud's cube like the box
+        // centroids, so that the FP32 errors scale with the cloud's size and not
+        // with its distance from the origin
         float xh = 0.f, yh = 0.f, zh = 0.f, xl = 0.f, yl = 0.f, zl = 0.f;
         if (valid) {
-            double X = a.x[t], Y = a.y[t], Z = a.z[t];
+            const double* cc = a.cubes[ck.z].c;
+            double X = a.x[t] - cc[0], Y = a.y[t] - cc[1], Z = a.z[t] - cc[2];
             xh = (float)X; yh = (float)Y; zh = (float)Z;
             xl = (float)(X - (double)xh); yl = (float)(Y - (double)yh); zl = (float)(Z - (double)zh);
         }
@@ -659,7 +662,8 @@ __global__ void k_mac_prepare(Tree t, const Cube* __restrict__ cube, double thet
     for (int nd = blockIdx.x * blockDim.x + threadIdx.x; nd < nn; nd += gridDim.x * blockDim.x) {
         double* m = t.mom + (size_t)nd * kMom;
         int dl = t.depth_leaf[nd];
-        const double L = cube[t.cloud ? t.cloud[t.info[nd].x] : 0].L;
+        const Cube& cb = cube[t.cloud ? t.cloud[t.info[nd].x] : 0];
+        const double L = cb.L;
         double s = ldexp(L, -(dl & 255));
         double r2;
         if (theta > 0.0) {
@@ -672,12 +676,14 @@ __global__ void k_mac_prepare(Tree t, const Cube* __restrict__ cube, double thet
         if (want_f32) {
             int4 inf = t.info[nd];
             float4* r = t.f32 + (size_t)nd * kF32;
-            // the centroid enters negated (x_t - c as a sum), the trace term of
-            // the expansion as one value
-            float chx = (float)m[0], chy = (float)m[1], chz = (float)m[2];
+            // the centroid, relative to the cube's centre as the walk's targets are,
+            // enters negated (x_t - c as a sum); the trace term of the expansion as
+            // one value
+            const double ux = m[0] - cb.c[0], uy = m[1] - cb.c[1], uz = m[2] - cb.c[2];
+            float chx = (float)ux, chy = (float)uy, chz = (float)uz;
             r[0] = make_float4(-chx, -chy, -chz, (float)r2);
-            r[1] = make_float4((float)((double)chx - m[0]), (float)((double)chy - m[1]),
-                               (float)((double)chz - m[2]), __int_as_float(inf.z));
+            r[1] = make_float4((float)((double)chx - ux), (float)((double)chy - uy),
+                               (float)((double)chz - uz), __int_as_float(inf.z));
             const float qxx = (float)m[MQ], qyy = (float)m[MQ + 3], qzz = (float)m[MQ + 5];
             r[2] = make_float4(-0.5f * ((qxx + qyy) + qzz),
                                __int_as_float((dl & 256) ? inf.y : -1), (float)m[MM],

@@ -171,6 +171,26 @@ def test_force_fp32c(U, orc, n, sigma, seed, leaf_cap, theta):
         assert (got <= np.maximum(np.quantile(tree_err, 0.99), 2 * own)).all(), got
 
 
+@pytest.mark.parametrize("shift", [0.0, 1.0e3, -3.0e4])
+def test_force_fp32c_translated_cloud(U, orc, shift):
+    """The FP32C walk's accuracy does not depend on where the cloud sits: a
+    cloud moved far from the origin meets the same bar against the oracle tree
+    (the walk's FP32 coordinates are taken relative to the cloud's cube)."""
+    c = gaussian_cloud(8192, 2.0, 17)
+    pos = c.pos + np.array([shift, 0.5 * shift, -shift])
+    eps, theta = 0.01, 0.5
+    T = orc.Tree(pos, c.species, c.q, leaf_cap=16)
+    E, phi, npp, nmp = T.force(theta, eps, nthreads=4, counts=True)
+    a_ref = E * (c.q[c.species] / c.m[c.species])[:, None]
+    with U.Context(c.n, c.q, c.m, leaf_cap=16, precision=U.UCP_FP32C) as ctx:
+        ctx.set_state(pos, c.vel, c.species)
+        acc, ph = ctx.tree_force(theta, eps)
+        gp, gm = ctx.get_counts()
+    assert rel_rms(acc, a_ref) <= 1e-5, rel_rms(acc, a_ref)
+    assert rel_rms(ph, phi) <= 1e-5, rel_rms(ph, phi)
+    assert np.count_nonzero((gp != npp) | (gm != nmp)) <= 2 + c.n // 1000
+
+
 def test_force_edge_cases(U, orc):
     eps = 0.05
     # one particle: no force, no potential
