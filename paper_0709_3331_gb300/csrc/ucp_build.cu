@@ -675,16 +675,23 @@ k_topo_emit(const unsigned long long* __restrict__ K, int n, int leaf_cap,
     int dmax = 0;
     for (int j = 0; j < c; ++j) {
         int d = d0 + j;
-        int e = -1;
-        if (kWin && j == c - 1) {
-            // the leaf: its end within the window, else (a bigger depth-cap box) search
-            const int li = threadIdx.x + kTopoWin;
-            for (int m = 1; m <= leaf_cap && e < 0; ++m)
-                if (fd[li + m] <= d) e = i + m;
+        // the boxes above the last one at this position hold more than leaf_cap
+        // particles (the count stops at the first that does not): twigs, whose end
+        // and skip index are their last child's, filled in by the moments' bottom-up
+        // sweep; only the last box's end is looked up here
+        int e = -1, nx = -1;
+        bool leaf = false;
+        if (j == c - 1) {
+            if (kWin) {
+                // the leaf: its end within the window, else (a bigger depth-cap box) search
+                const int li = threadIdx.x + kTopoWin;
+                for (int m = 1; m <= leaf_cap && e < 0; ++m)
+                    if (fd[li + m] <= d) e = i + m;
+            }
+            if (e < 0) e = box_end(K, hi, i, d);
+            leaf = (e - i <= leaf_cap) || d == kMaxDepth;
+            nx = e < n ? off[e] : nn;
         }
-        if (e < 0) e = box_end(K, hi, i, d);
-        bool leaf = (e - i <= leaf_cap) || d == kMaxDepth;
-        int nx = e < n ? off[e] : nn;
         if (node >= t.cap) break;  // cannot happen: the capacity bounds the box count
         unsigned long long pre = prefix_at(K[i], d);
         t.info[node] = make_int4(i, e, nx, parent);
@@ -842,12 +849,22 @@ __device__ __forceinline__ void sweep_up(const Tree& t, int node, Combine combin
 {
     int p = t.info[node].w;
     while (p >= 0) {
-        int nch = 0;
+        int nch = 0, last = -1;
 #pragma unroll
-        for (int o = 0; o < 8; ++o) nch += t.child8[(size_t)p * 8 + o] >= 0;
+        for (int o = 0; o < 8; ++o) {
+            const int ch = t.child8[(size_t)p * 8 + o];
+            nch += ch >= 0;
+            if (ch >= 0) last = ch;
+        }
         // this box's records are published with its arrival; the last arrival
         // sees every sibling's
         if (atomic_add_acq_rel(&t.arrive[p], 1) + 1 < nch) return;
+        // a twig ends where its last child (in octant order, so last in pre-order)
+        // ends, and skips to where that child skips
+        const int4 lc = __ldcg(&t.info[last]);
+        int* ip = reinterpret_cast<int*>(&t.info[p]);
+        ip[1] = lc.y;
+        ip[2] = lc.z;
         combine(p, t.depth_leaf[p] & 255);
         p = t.info[p].w;
     }
